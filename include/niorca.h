@@ -1,0 +1,129 @@
+/*
+ * niorca.h -- C ABI of the GB300 NI-ORCA library (libniorca.so).
+ *
+ * The library computes, for every vertex x of a simple undirected graph
+ * G = (V, E), the counts psi_0(x) .. psi_14(x) of the 15 orbits of the
+ * non-induced connected graphlets on 2, 3 and 4 vertices (Sec. 3, Defs. 3-5;
+ * the output o_0 .. o_14 of Algorithm 1). It follows the paper's three
+ * stages: per-edge triangles (Stage I, Algorithm 1), 4-cliques (Stage II,
+ * Algorithm 2) and the orbit equations over the f* variables of Table 1
+ * (Stage III, Sec. 5 and the Appendix). Every count is an exact int64.
+ *
+ * Orbit numbering (the paper's Fig. 2 is not in its text; the numbering
+ * under which all its equations hold): 0 edge; 1 / 2 end / middle of a path
+ * on 3 vertices; 3 triangle; 4 / 5 end / interior of a path on 4 vertices;
+ * 6 / 7 leaf / centre of a 3-star; 8 4-cycle; 9 / 10 / 11 vertex of degree
+ * 1 / 2 / 3 of the paw (tailed triangle); 12 / 13 vertex of degree 2 / 3 of
+ * the diamond; 14 K4.
+ *
+ * Conventions for every call:
+ *   - Graph input is CSR in caller-owned DEVICE memory: rowptr int32[n+1]
+ *     with rowptr[0] = 0 and rowptr[n] = m; colidx int32[m]; m = 2|E| (each
+ *     undirected edge appears in both rows). Every row is strictly increasing,
+ *     has no self-loop, and the graph is symmetric (Sec. 3: a simple graph).
+ *   - Output is caller-owned DEVICE memory, int64 out[n * 15], row-major:
+ *     out[v * 15 + k] = psi_k(v). It is fully overwritten.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
+ *     only enqueue work; they never synchronise the stream. Results are valid
+ *     once the stream has reached the end of the call's work.
+ *   - Argument errors are returned synchronously and nothing is enqueued.
+ *     Errors found on the device (malformed CSR, too large a degree) are
+ *     recorded in a per-device status word, read by niorca_last_status();
+ *     after such an error `out` is unspecified. Malformed input never makes
+ *     a kernel access memory outside the given arrays.
+ *   - Work memory is taken from a library-owned, stream-ordered pool on the
+ *     current device and returned to it when the stream reaches the end of
+ *     the call; the pool keeps freed memory for reuse.
+ *   - Sizes: n < 2^31, m < 2^31; the largest degree must be at most 2^20,
+ *     which bounds every intermediate below 2^62 (else NIORCA_EOVERFLOW).
+ */
+#ifndef NIORCA_H
+#define NIORCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NIORCA_OK = 0,
+    NIORCA_EINVAL = 1,      /* bad argument, or CSR offsets out of range      */
+    NIORCA_ENOTSIMPLE = 2,  /* self-loop, unsorted/duplicate row, asymmetric   */
+    NIORCA_EOVERFLOW = 3,   /* a degree above 2^20: counts may exceed int64    */
+    NIORCA_ENOMEM = 4,      /* the work memory could not be allocated          */
+    NIORCA_ECUDA = 5,       /* a CUDA call failed (launch, pool, event)        */
+    NIORCA_ETIMEOUT = 6     /* a bounded device wait gave up                   */
+} niorca_status;
+
+/*
+ * Orbit counts of one graph (Algorithm 1: Stages I, II and III).
+ *   rowptr  device int32[n + 1]   CSR offsets, rowptr[0] = 0, rowptr[n] = m
+ *   colidx  device int32[m]       neighbours, each row strictly increasing
+ *   n       number of vertices, 0 <= n < 2^31
+ *   m       number of CSR entries (2|E|), 0 <= m < 2^31
+ *   out     device int64[n * 15]  psi_k(v) at out[v * 15 + k]
+ *   stream  cudaStream_t to enqueue on
+ * Returns NIORCA_EINVAL for null pointers with n > 0 or m > 0, negative or
+ * too large sizes; NIORCA_ENOMEM / NIORCA_ECUDA if enqueueing failed.
+ */
+niorca_status niorca_count(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                           int64_t *out, void *stream);
+
+/*
+ * Orbit counts of many independent graphs in one call (the same stages for
+ * each graph; graphs are packed back to back).
+ *   rowptr      device int32[total_n + 1]: the concatenation of every
+ *               graph's offsets rowptr_g[0..n_g-1], each shifted by
+ *               edge_offset[g], followed by total_m. Equivalently the CSR of
+ *               the disjoint union of the graphs.
+ *   colidx      device int32[total_m]: column ids LOCAL to each graph
+ *               (0 <= colidx < n_g).
+ *   vtx_offset  device int64[num_graphs + 1]: prefix sums of n_g.
+ *   edge_offset device int64[num_graphs + 1]: prefix sums of m_g.
+ *   num_graphs  number of graphs (>= 0).
+ *   total_n, total_m  vtx_offset[num_graphs] and edge_offset[num_graphs].
+ *   out         device int64[total_n * 15]; graph g's vertex v at row
+ *               vtx_offset[g] + v.
+ * Each graph is subject to the limits of niorca_count. The results are
+ * identical to counting each graph alone.
+ */
+niorca_status niorca_count_batch(const int32_t *rowptr, const int32_t *colidx, const int64_t *vtx_offset,
+                                 const int64_t *edge_offset, int32_t num_graphs, int64_t total_n,
+                                 int64_t total_m, int64_t *out, void *stream);
+
+/*
+ * Full simple-graph check of a CSR (Sec. 3: G is simple and undirected):
+ * offsets in range, rows strictly increasing, no self-loops, and every
+ * entry (x, y) matched by (y, x). Enqueued on `stream`; the verdict is
+ * read with niorca_last_status(). niorca_count itself checks everything
+ * but symmetry.
+ */
+niorca_status niorca_validate(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m, void *stream);
+
+/*
+ * Synchronises `stream`, then returns and clears the device status word of
+ * the current device: the first error that any call recorded on the device
+ * since the previous read (NIORCA_OK if none), or NIORCA_ECUDA if the
+ * stream itself reports an error.
+ */
+niorca_status niorca_last_status(void *stream);
+
+/* Bytes of work memory one niorca_count call of this size takes. */
+size_t niorca_workspace_bytes(int32_t n, int64_t m);
+
+/* Work memory of a niorca_count_batch call of this size. */
+size_t niorca_batch_workspace_bytes(int32_t num_graphs, int64_t total_n, int64_t total_m);
+
+/* Human-readable name of a status code (static string). */
+const char *niorca_status_string(niorca_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int32_t niorca_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NIORCA_H */

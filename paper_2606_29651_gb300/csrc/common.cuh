@@ -1,0 +1,178 @@
+// common.cuh -- device helpers shared by the NI-ORCA kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace niorca {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int NCLASS = 128;  // degree classes used for the relabel order
+
+// Device status bits (one per niorca_status code, bit k = code k).
+enum : int {
+    ST_EINVAL = 1 << 1,
+    ST_ENOTSIMPLE = 1 << 2,
+    ST_EOVERFLOW = 1 << 3,
+    ST_ETIMEOUT = 1 << 6,
+};
+
+// Largest degree for which every intermediate of the orbit solve stays
+// below 2^62 in int64 (each term is at most d_max^3 plus lower terms).
+constexpr int MAX_DEGREE = 1 << 20;
+
+// Degree class: exact for d < 8, then four classes per octave (the top two
+// bits below the leading one). Classes are monotone in d, 0 <= class < 120.
+__host__ __device__ __forceinline__ int deg_class(int d) {
+    if (d < 8) return d < 0 ? 0 : d;
+#ifdef __CUDA_ARCH__
+    int e = 31 - __clz(d);
+#else
+    int e = 31 - __builtin_clz((unsigned)d);
+#endif
+    return 8 + (e - 3) * 4 + ((d >> (e - 2)) & 3);
+}
+
+// Per-vertex accumulators, indexed by the relabelled (degree-ordered) id.
+// S1 and A1 come first: the orbit solve gathers them over neighbours.
+struct __align__(16) VAcc {
+    long long S1;   // sum of neighbour degrees
+    long long A1;   // sum over incident edges of t_xy (= 2 * triangles at x)
+    long long P6;   // sum over neighbours of C(d_y - 1, 2)
+    long long A2;   // sum of t_xy^2
+    long long A3;   // sum of t_xy * d_y
+    long long D12;  // sum over triangles {x,y,z} of (t_yz - 1)   (f_12^14)
+    long long K4;   // 4-cliques containing x                      (psi_14)
+    long long C4;   // 4-cycles through x                          (psi_8)
+};
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_inclusive_scan(T v) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T t = __shfl_up_sync(FULL, v, o);
+        if (lane_id() >= o) v += t;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+__device__ __forceinline__ void add64(long long *p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+
+__device__ __forceinline__ void set_status(int *status, int bits) { atomicOr(status, bits); }
+
+// Multiplicative hash of a vertex id into a power-of-two table.
+__device__ __forceinline__ unsigned hash_slot(int key, unsigned mask) {
+    unsigned h = static_cast<unsigned>(key) * 0x9E3779B1u;
+    return (h ^ (h >> 16)) & mask;
+}
+
+// Open-addressing set of vertex ids with a value (an index) per key.
+// Keys are -1 when empty. Capacity is a power of two, at least twice the
+// number of keys inserted, so probes always end.
+__device__ __forceinline__ void hset_insert(int *keys, int *vals, unsigned mask, int key, int val) {
+    unsigned s = hash_slot(key, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        int prev = atomicCAS(&keys[s], -1, key);
+        if (prev == -1 || prev == key) {
+            vals[s] = val;
+            return;
+        }
+        s = (s + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ int hset_find(const int *keys, const int *vals, unsigned mask, int key) {
+    unsigned s = hash_slot(key, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        int k = keys[s];
+        if (k == key) return vals[s];
+        if (k == -1) return -1;
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
+// Counting table keyed by vertex id: increments the count of `key`.
+__device__ __forceinline__ bool hcount_add(int *keys, int *cnts, unsigned mask, int key) {
+    unsigned s = hash_slot(key, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        int k = keys[s];
+        if (k == key) {
+            atomicAdd(&cnts[s], 1);
+            return true;
+        }
+        if (k == -1) {
+            int prev = atomicCAS(&keys[s], -1, key);
+            if (prev == -1 || prev == key) {
+                atomicAdd(&cnts[s], 1);
+                return true;
+            }
+        }
+        s = (s + 1) & mask;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int hcount_get(const int *keys, const int *cnts, unsigned mask, int key) {
+    unsigned s = hash_slot(key, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        int k = keys[s];
+        if (k == key) return cnts[s];
+        if (k == -1) return 0;
+        s = (s + 1) & mask;
+    }
+    return 0;
+}
+
+// First position p in [lo, hi) with a[p] >= key (a sorted ascending).
+__device__ __forceinline__ int lower_bound(const int *a, int lo, int hi, int key) {
+    while (lo < hi) {
+        int mid = lo + ((hi - lo) >> 1);
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Position of key in sorted a[lo, hi), or -1.
+__device__ __forceinline__ int find_sorted(const int *a, int lo, int hi, int key) {
+    int p = lower_bound(a, lo, hi, key);
+    return (p < hi && a[p] == key) ? p : -1;
+}
+
+__host__ __device__ __forceinline__ unsigned next_pow2(unsigned v) {
+    v--;
+    v |= v >> 1; v |= v >> 2; v |= v >> 4; v |= v >> 8; v |= v >> 16;
+    return v + 1;
+}
+
+// Work-memory views of one counting call (all device pointers).
+struct Graph {
+    int n;              // vertices
+    int m;              // CSR entries (2|E|)
+    const int *nrow;    // relabelled offsets, n + 1
+    const int *ncol;    // relabelled neighbours, rows ascending
+    const int *split;   // split[u]: first position of row u holding an id > u
+};
+
+}  // namespace niorca

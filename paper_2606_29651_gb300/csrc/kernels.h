@@ -1,0 +1,54 @@
+// kernels.h -- host-side launchers of the NI-ORCA stages (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace niorca {
+
+// Per-call work memory, carved from one pool allocation.
+struct Work {
+    int n = 0, m = 0;
+    int ntiles = 0;          // relabel tiles of RL_TILE vertices
+    int2 *vinfo = nullptr;   // old id -> (new id, degree)
+    int *perm = nullptr;     // new id -> old id
+    int *chist = nullptr;    // class histogram, NCLASS x ntiles (class-major)
+    int *coff = nullptr;     // exclusive scan of chist
+    int *nrow = nullptr;     // relabelled offsets, n + 1
+    int *split = nullptr;    // first out-neighbour position of each row (also scan input)
+    int *ncol = nullptr;     // relabelled neighbours, m
+    int *tcnt = nullptr;     // triangle count of each out-entry (u, v), u < v; m
+    VAcc *vacc = nullptr;    // per-vertex accumulators, n
+    int *scan_part = nullptr;// scan block partials
+    int *lists = nullptr;    // heavy-vertex lists, 4 x n
+    int *counters = nullptr; // list lengths and flags, 16 ints
+    int *c4dense = nullptr;  // dense counting rows for the largest 4-cycle roots
+    int c4slots = 0;         // rows in c4dense (each n ints)
+    int *status = nullptr;   // device status word (not part of the carve)
+    int num_sms = 0;
+};
+
+// Indices into Work::counters.
+enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_GLOBAL = 3, CNT_DMAX = 4 };
+
+constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
+constexpr int SCAN_TILE = 4096;      // elements per scan block
+constexpr int LONG_ROW_CLASS = 32;   // deg_class(512): rows from here on get a CTA each
+constexpr int C4_SLOTS_MAX = 128;    // dense rows for the global 4-cycle tier
+
+size_t scan_partials(long long len);
+void launch_exclusive_scan(const int *in, int *out, long long len, bool write_total, int *part,
+                           cudaStream_t st);
+
+void launch_relabel(const int *rowptr, const int *colidx, Work &w, cudaStream_t st);
+void launch_stage1(Work &w, cudaStream_t st);
+void launch_stage2(Work &w, cudaStream_t st);
+void launch_cycle4(Work &w, cudaStream_t st);
+void launch_solve(Work &w, long long *out, cudaStream_t st);
+void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *status, int num_sms,
+                     cudaStream_t st);
+
+// Opt-in to large dynamic shared memory for every kernel that needs it.
+void configure_kernels();
+
+}  // namespace niorca

@@ -1,0 +1,231 @@
+// niorca_api.cu -- the C ABI (include/niorca.h): argument checks, per-device
+// state, work memory and the launch sequence of the three stages.
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/niorca.h"
+#include "kernels.h"
+
+namespace niorca {
+
+void configure_stage1();
+void configure_stage2();
+void configure_cycle4();
+void launch_batch_setup(const int *rowptr, const long long *vtx_offset, const long long *edge_offset, int num_graphs,
+                        int total_n, int2 *vrange, int *status, int num_sms, cudaStream_t st);
+void launch_relabel_batch(const int *rowptr, const int *colidx, const int2 *vrange, Work &w, cudaStream_t st);
+
+namespace {
+
+struct DeviceState {
+    bool ready = false;
+    cudaMemPool_t pool = nullptr;
+    int *status = nullptr;
+    int num_sms = 0;
+};
+
+constexpr int MAX_DEVICES = 64;
+DeviceState g_dev[MAX_DEVICES];
+std::mutex g_mu;
+
+niorca_status device_state(DeviceState **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return NIORCA_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &d = g_dev[dev];
+    if (!d.ready) {
+        if (cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return NIORCA_ECUDA;
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&d.pool, &props) != cudaSuccess) return NIORCA_ECUDA;
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (cudaMalloc(&d.status, sizeof(int)) != cudaSuccess) return NIORCA_ENOMEM;
+        if (cudaMemset(d.status, 0, sizeof(int)) != cudaSuccess) return NIORCA_ECUDA;
+        configure_stage1();
+        configure_stage2();
+        configure_cycle4();
+        if (cudaGetLastError() != cudaSuccess) return NIORCA_ECUDA;
+        d.ready = true;
+    }
+    *out = &d;
+    return NIORCA_OK;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t vinfo, perm, chist, coff, nrow, split, ncol, tcnt, vacc, scan_part, lists, counters, c4dense, vrange;
+    size_t total;
+    int ntiles, c4slots;
+};
+
+Layout plan(long long n, long long m, int num_sms, bool batch) {
+    Layout L;
+    L.ntiles = (int)((n + RL_TILE - 1) / RL_TILE);
+    // the dense 4-cycle rows are only reachable by a root with more than
+    // 8192 wedges, which needs m above that
+    L.c4slots = m > 8192 ? (num_sms < 64 ? num_sms : 64) : 0;
+    const long long nt = L.ntiles;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + (bytes ? bytes : 1)); return at; };
+    L.vinfo = take(8 * n);
+    L.perm = take(4 * n);
+    L.chist = take(4 * NCLASS * nt);
+    L.coff = take(4 * NCLASS * nt);
+    L.nrow = take(4 * (n + 1));
+    L.split = take(4 * n);
+    L.ncol = take(4 * m);
+    L.tcnt = take(4 * m);
+    L.vacc = take(sizeof(VAcc) * n);
+    const size_t sp1 = scan_partials(NCLASS * nt), sp2 = scan_partials(n);
+    L.scan_part = take(4 * (sp1 > sp2 ? sp1 : sp2));
+    L.lists = take(4 * 4 * n);
+    L.counters = take(4 * 16);
+    L.c4dense = take(4 * (size_t)L.c4slots * n);
+    L.vrange = batch ? take(8 * n) : 0;
+    L.total = o;
+    return L;
+}
+
+niorca_status check_launch() {
+    return cudaPeekAtLastError() == cudaSuccess ? NIORCA_OK : NIORCA_ECUDA;
+}
+
+// Runs the whole pipeline on one (possibly union) graph.
+niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long *out, cudaStream_t st,
+                  const long long *vtx_offset, const long long *edge_offset, int num_graphs) {
+    DeviceState *ds = nullptr;
+    niorca_status s = device_state(&ds);
+    if (s != NIORCA_OK) return s;
+    const bool batch = vtx_offset != nullptr;
+    const Layout L = plan(n, m, ds->num_sms, batch);
+    void *base = nullptr;
+    if (cudaMallocFromPoolAsync(&base, L.total, ds->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        return NIORCA_ENOMEM;
+    }
+    unsigned char *b = static_cast<unsigned char *>(base);
+    Work w;
+    w.n = n;
+    w.m = m;
+    w.ntiles = L.ntiles;
+    w.vinfo = reinterpret_cast<int2 *>(b + L.vinfo);
+    w.perm = reinterpret_cast<int *>(b + L.perm);
+    w.chist = reinterpret_cast<int *>(b + L.chist);
+    w.coff = reinterpret_cast<int *>(b + L.coff);
+    w.nrow = reinterpret_cast<int *>(b + L.nrow);
+    w.split = reinterpret_cast<int *>(b + L.split);
+    w.ncol = reinterpret_cast<int *>(b + L.ncol);
+    w.tcnt = reinterpret_cast<int *>(b + L.tcnt);
+    w.vacc = reinterpret_cast<VAcc *>(b + L.vacc);
+    w.scan_part = reinterpret_cast<int *>(b + L.scan_part);
+    w.lists = reinterpret_cast<int *>(b + L.lists);
+    w.counters = reinterpret_cast<int *>(b + L.counters);
+    w.c4dense = reinterpret_cast<int *>(b + L.c4dense);
+    w.c4slots = L.c4slots;
+    w.status = ds->status;
+    w.num_sms = ds->num_sms;
+    cudaMemsetAsync(w.counters, 0, 4 * 16, st);
+    if (batch) {
+        int2 *vrange = reinterpret_cast<int2 *>(b + L.vrange);
+        launch_batch_setup(rowptr, vtx_offset, edge_offset, num_graphs, n, vrange, ds->status, ds->num_sms, st);
+        launch_relabel_batch(rowptr, colidx, vrange, w, st);
+    } else {
+        launch_relabel(rowptr, colidx, w, st);
+    }
+    launch_stage1(w, st);
+    launch_stage2(w, st);
+    launch_cycle4(w, st);
+    launch_solve(w, out, st);
+    s = check_launch();
+    cudaFreeAsync(base, st);
+    return s;
+}
+
+}  // namespace
+}  // namespace niorca
+
+using namespace niorca;
+
+extern "C" niorca_status niorca_count(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                                      int64_t *out, void *stream) {
+    if (n < 0 || m < 0 || m > INT32_MAX) return NIORCA_EINVAL;
+    if (n == 0) return m == 0 ? NIORCA_OK : NIORCA_EINVAL;
+    if (!rowptr || !out || (m > 0 && !colidx)) return NIORCA_EINVAL;
+    return run(rowptr, colidx, n, (int)m, reinterpret_cast<long long *>(out), static_cast<cudaStream_t>(stream),
+               nullptr, nullptr, 0);
+}
+
+extern "C" niorca_status niorca_count_batch(const int32_t *rowptr, const int32_t *colidx, const int64_t *vtx_offset,
+                                            const int64_t *edge_offset, int32_t num_graphs, int64_t total_n,
+                                            int64_t total_m, int64_t *out, void *stream) {
+    if (num_graphs < 0 || total_n < 0 || total_m < 0 || total_n > INT32_MAX - 1 || total_m > INT32_MAX)
+        return NIORCA_EINVAL;
+    if (num_graphs == 0 || total_n == 0) return total_m == 0 ? NIORCA_OK : NIORCA_EINVAL;
+    if (!rowptr || !out || !vtx_offset || !edge_offset || (total_m > 0 && !colidx)) return NIORCA_EINVAL;
+    return run(rowptr, colidx, (int)total_n, (int)total_m, reinterpret_cast<long long *>(out),
+               static_cast<cudaStream_t>(stream), reinterpret_cast<const long long *>(vtx_offset),
+               reinterpret_cast<const long long *>(edge_offset), num_graphs);
+}
+
+extern "C" niorca_status niorca_validate(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                                         void *stream) {
+    if (n < 0 || m < 0 || m > INT32_MAX) return NIORCA_EINVAL;
+    if (n == 0) return m == 0 ? NIORCA_OK : NIORCA_EINVAL;
+    if (!rowptr || (m > 0 && !colidx)) return NIORCA_EINVAL;
+    DeviceState *ds = nullptr;
+    niorca_status s = device_state(&ds);
+    if (s != NIORCA_OK) return s;
+    launch_validate(rowptr, colidx, n, (int)m, ds->status, ds->num_sms, static_cast<cudaStream_t>(stream));
+    return check_launch();
+}
+
+extern "C" niorca_status niorca_last_status(void *stream) {
+    DeviceState *ds = nullptr;
+    niorca_status s = device_state(&ds);
+    if (s != NIORCA_OK) return s;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return NIORCA_ECUDA;
+    int bits = 0;
+    if (cudaMemcpy(&bits, ds->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NIORCA_ECUDA;
+    if (bits && cudaMemset(ds->status, 0, sizeof(int)) != cudaSuccess) return NIORCA_ECUDA;
+    const niorca_status order[] = {NIORCA_EINVAL, NIORCA_ENOTSIMPLE, NIORCA_EOVERFLOW, NIORCA_ETIMEOUT};
+    for (niorca_status c : order)
+        if (bits & (1 << c)) return c;
+    return NIORCA_OK;
+}
+
+extern "C" size_t niorca_workspace_bytes(int32_t n, int64_t m) {
+    if (n <= 0 || m < 0) return 0;
+    int sms = 152;
+    DeviceState *ds = nullptr;
+    if (device_state(&ds) == NIORCA_OK) sms = ds->num_sms;
+    return plan(n, m, sms, false).total;
+}
+
+extern "C" size_t niorca_batch_workspace_bytes(int32_t num_graphs, int64_t total_n, int64_t total_m) {
+    if (num_graphs <= 0 || total_n <= 0 || total_m < 0) return 0;
+    int sms = 152;
+    DeviceState *ds = nullptr;
+    if (device_state(&ds) == NIORCA_OK) sms = ds->num_sms;
+    return plan(total_n, total_m, sms, true).total;
+}
+
+extern "C" const char *niorca_status_string(niorca_status s) {
+    switch (s) {
+    case NIORCA_OK: return "ok";
+    case NIORCA_EINVAL: return "invalid argument or CSR offsets";
+    case NIORCA_ENOTSIMPLE: return "graph is not simple (self-loop, unsorted or duplicate row, asymmetric)";
+    case NIORCA_EOVERFLOW: return "degree above 2^20: counts may overflow int64";
+    case NIORCA_ENOMEM: return "out of device memory";
+    case NIORCA_ECUDA: return "CUDA error";
+    case NIORCA_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+extern "C" int32_t niorca_version(void) { return 100; }

@@ -1,0 +1,116 @@
+// solve.cu -- Stage III-b: the orbit equations (Sec. 5 and the Appendix).
+//
+// One warp per vertex x gathers, over N(x), the neighbours' S1 (sum of their
+// neighbours' degrees) and A1 (twice their triangle count); together with
+// x's own accumulators this gives the nine f* variables of Table 1 in closed
+// form (each is a sum over the substructures of Fig. 3 around x):
+//   f_12^14 = D12
+//   f_10^13 = A3 - 2 A1 - 2 D12
+//   f_13^14 = A2 - A1
+//   f_11^13 = (d - 1) A1 - A2
+//   f_5^8   = (d - 1)(S1 - d) - (d - 1) A1 - (A3 - A1) + A2
+//   f_6^9   = 2 P6 - 2 A3 + 3 A1 + A2
+//   f_9^12  = 2 sum_y T(y) - 2 A1 - 2 D12
+//   f_4^8   = sum_y S1(y) - S1 - 2 sum_y T(y) - d (d - 1) + A1 - f_10^13
+//   f_8^12  = 2 C4 - f_13^14
+// with d = deg x, T = A1 / 2 and sum_y over N(x). The equations of the paper
+// then give psi_4 .. psi_13; psi_0 = d, psi_1 = S1 - d (paths x-y-z),
+// psi_2 = C(d, 2), psi_3 = T, psi_7 = C(d, 3), psi_14 = K4. Rows are written
+// in the caller's vertex ids.
+#include "kernels.h"
+
+namespace niorca {
+
+__device__ __forceinline__ void orbit_equations(long long d, const VAcc &a, long long sS1, long long sT,
+                                                long long *psi) {
+    const long long A1 = a.A1, A2 = a.A2, A3 = a.A3, S1 = a.S1, D12 = a.D12;
+    const long long f12 = D12;
+    const long long f10 = A3 - 2 * A1 - 2 * D12;
+    const long long f13 = A2 - A1;
+    const long long f11 = (d - 1) * A1 - A2;
+    const long long f5 = (d - 1) * (S1 - d) - (d - 1) * A1 - (A3 - A1) + A2;
+    const long long f6 = 2 * a.P6 - 2 * A3 + 3 * A1 + A2;
+    const long long f9 = 2 * sT - 2 * A1 - 2 * D12;
+    const long long f4 = sS1 - S1 - 2 * sT - d * (d - 1) + A1 - f10;
+    const long long f8 = 2 * a.C4 - f13;
+    psi[0] = d;
+    psi[1] = S1 - d;
+    psi[2] = d * (d - 1) / 2;
+    psi[3] = A1 / 2;
+    psi[4] = 2 * f12 + f4 + f10 + f9;          // Appendix, o4
+    psi[5] = 2 * f12 + f5 + f10 + f11;         // Appendix, o5
+    psi[6] = (f6 - f13) / 2 + f10 + 2 * f12;   // Appendix, o6
+    psi[7] = d * (d - 1) / 2 * (d - 2) / 3;    // Appendix, o7 = C(psi_0, 3)
+    psi[8] = (f13 + f8) / 2;                   // Appendix, o8
+    psi[9] = f12 + f9 / 2;                     // Appendix, o9
+    psi[10] = f10 + 2 * f12;                   // Eq. o10
+    psi[11] = (f11 + f13) / 2;                 // Eq. o11
+    psi[12] = f12;                             // Eq. o12
+    psi[13] = f13 / 2;                         // Eq. o13
+    psi[14] = a.K4;                            // K4[x] (Stage II)
+}
+
+__global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const int *perm, long long *out) {
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int x = gw; x < g.n; x += nw) {
+        const int b = g.nrow[x], e = g.nrow[x + 1];
+        long long sS1 = 0, sA1 = 0;
+        for (int p = b + lane; p < e; p += 32) {
+            const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[p]]);
+            sS1 += sa.x;
+            sA1 += sa.y;
+        }
+        sS1 = warp_sum(sS1);
+        sA1 = warp_sum(sA1);
+        if (lane < 15) {
+            const VAcc a = vacc[x];
+            long long psi[15];
+            orbit_equations(e - b, a, sS1, sA1 / 2, psi);
+            long long v = psi[0];
+#pragma unroll
+            for (int k = 1; k < 15; ++k)
+                if (lane == k) v = psi[k];
+            out[(size_t)perm[x] * 15 + lane] = v;
+        }
+    }
+}
+
+void launch_solve(Work &w, long long *out, cudaStream_t st) {
+    Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
+    k_solve<<<w.num_sms * 8, 256, 0, st>>>(g, w.vacc, w.perm, out);
+}
+
+// Full simple-graph check: offsets, strictly increasing rows, no self-loops,
+// and symmetry (every (x, y) has its (y, x)), one warp per row.
+__global__ void __launch_bounds__(256) k_validate(const int *rowptr, const int *colidx, int n, int m, int *status) {
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    int bad = 0;
+    for (int x = gw; x < n; x += nw) {
+        const int a = rowptr[x], b = rowptr[x + 1];
+        if (a < 0 || b < a || b > m || (x == 0 && a != 0) || (x == n - 1 && b != m)) {
+            bad |= ST_EINVAL;
+            continue;
+        }
+        for (int p = a + lane; p < b; p += 32) {
+            const int y = colidx[p];
+            if (y < 0 || y >= n) { bad |= ST_EINVAL; continue; }
+            if (y == x || (p > a && colidx[p - 1] >= y)) { bad |= ST_ENOTSIMPLE; continue; }
+            const int ya = rowptr[y], yb = rowptr[y + 1];
+            if (ya < 0 || yb < ya || yb > m) { bad |= ST_EINVAL; continue; }
+            if (find_sorted(colidx, ya, yb, x) < 0) bad |= ST_ENOTSIMPLE;
+        }
+    }
+    bad = __reduce_or_sync(FULL, bad);
+    if (lane == 0 && bad) set_status(status, bad);
+}
+
+void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *status, int num_sms, cudaStream_t st) {
+    if (n <= 0) return;
+    k_validate<<<num_sms * 8, 256, 0, st>>>(rowptr, colidx, n, m, status);
+}
+
+}  // namespace niorca

@@ -1,0 +1,291 @@
+// stage1.cu -- Stage I (per-edge triangle counts, Algorithm 1) fused with
+// Stage II (K4 per vertex, Algorithm 2).
+//
+// In the relabelled graph every triangle u < v < w is found once, at its
+// lowest vertex u, as w in N+(u) ∩ N+(v) (Algorithm 2 enumerates the same
+// way with ids). For a root u the kernel loads N+(u) into a shared-memory
+// hash table, streams N+(v) of every v in N+(u) across the lanes of a warp
+// (the lists of several v are concatenated so that every lane is busy) and
+// probes each element. A hit is a triangle (u, v, w):
+//   t(u,v) and t(u,w) are counted in shared memory and added once per root,
+//   t(v,w) is added to global memory at the position of w in row v.
+// The hits also fill R, the adjacency bit-matrix of N+(u) oriented upwards:
+// R[j] bit i <=> N+(u)[i] in N+(N+(u)[j]). A K4 u < v < w < x is then a
+// triangle (j, i) of R together with a common bit of R[j] and R[i], so the
+// K4 count of each triangle is popc(R[j] & R[i]) -- Algorithm 2's pairwise
+// test over `neigh` done as word-wide bit operations.
+#include "kernels.h"
+
+namespace niorca {
+
+// Index of the segment that holds element k of a warp's concatenation:
+// the last q with pre[q] <= k (segments of length 0 never qualify).
+__device__ __forceinline__ int seg_owner(const int *pre, int k) {
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ----------------------------------------------------------- warp tier
+
+constexpr int TW_MAXD = 64;   // out-degree handled by one warp
+constexpr int TW_WARPS = 8;
+
+struct TriWarpSmem {
+    int hk[2 * TW_MAXD];
+    int hv[2 * TW_MAXD];
+    int cnt[TW_MAXD];
+    int kc[TW_MAXD];
+    unsigned R[TW_MAXD][2];
+    int sst[32];
+    int spre[32];
+};
+
+__global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, VAcc *vacc, int *heavy,
+                                                            int *counters) {
+    __shared__ TriWarpSmem sm_all[TW_WARPS];
+    TriWarpSmem &S = sm_all[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int u = gw; u < g.n; u += nw) {
+        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        if (dp < 2) continue;
+        if (dp > TW_MAXD) {
+            if (lane == 0) heavy[atomicAdd(&counters[CNT_TRI_HEAVY], 1)] = u;
+            continue;
+        }
+        const unsigned mask = next_pow2(2 * dp) - 1;
+        for (int i = lane; i <= (int)mask; i += 32) S.hk[i] = -1;
+        for (int i = lane; i < TW_MAXD; i += 32) {
+            S.cnt[i] = 0;
+            S.kc[i] = 0;
+            S.R[i][0] = 0;
+            S.R[i][1] = 0;
+        }
+        __syncwarp();
+        for (int i = lane; i < dp; i += 32) hset_insert(S.hk, S.hv, mask, g.ncol[s + i], i);
+        const int umax = g.ncol[e - 1];
+        __syncwarp();
+        int found = 0;
+        for (int jb = 0; jb < dp - 1; jb += 32) {
+            const int j = jb + lane;
+            int len = 0, vs = 0;
+            if (j < dp - 1) {
+                const int v = g.ncol[s + j];
+                vs = g.split[v];
+                len = g.nrow[v + 1] - vs;
+            }
+            const int incl = warp_inclusive_scan(len);
+            S.sst[lane] = vs;
+            S.spre[lane] = incl - len;
+            const int total = __shfl_sync(FULL, incl, 31);
+            __syncwarp();
+            for (int kb = 0; kb < total; kb += 32) {
+                const int k = kb + lane;
+                if (k >= total) break;
+                const int q = seg_owner(S.spre, k);
+                const int pos = S.sst[q] + (k - S.spre[q]);
+                const int w = g.ncol[pos];
+                if (w > umax) continue;
+                const int i = hset_find(S.hk, S.hv, mask, w);
+                if (i < 0) continue;
+                const int jj = jb + q;
+                atomicAdd(&S.cnt[jj], 1);
+                atomicAdd(&S.cnt[i], 1);
+                atomicAdd(&tcnt[pos], 1);
+                atomicOr(&S.R[jj][i >> 5], 1u << (i & 31));
+                found = 1;
+            }
+            __syncwarp();
+        }
+        if (!__any_sync(FULL, found)) continue;
+        for (int i = lane; i < dp; i += 32)
+            if (S.cnt[i]) atomicAdd(&tcnt[s + i], S.cnt[i]);
+        long long ku = 0;
+        for (int j = lane; j < dp; j += 32) {
+            const unsigned rj0 = S.R[j][0], rj1 = S.R[j][1];
+            for (int wd = 0; wd < 2; ++wd) {
+                unsigned bits = wd ? rj1 : rj0;
+                while (bits) {
+                    const int i = wd * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    unsigned x0 = rj0 & S.R[i][0], x1 = rj1 & S.R[i][1];
+                    const int k = __popc(x0) + __popc(x1);
+                    if (!k) continue;
+                    ku += k;
+                    atomicAdd(&S.kc[j], k);
+                    atomicAdd(&S.kc[i], k);
+                    while (x0) { atomicAdd(&S.kc[__ffs(x0) - 1], 1); x0 &= x0 - 1; }
+                    while (x1) { atomicAdd(&S.kc[32 + __ffs(x1) - 1], 1); x1 &= x1 - 1; }
+                }
+            }
+        }
+        ku = warp_sum(ku);
+        __syncwarp();
+        if (lane == 0 && ku) add64(&vacc[u].K4, ku);
+        for (int i = lane; i < dp; i += 32)
+            if (S.kc[i]) add64(&vacc[g.ncol[s + i]].K4, S.kc[i]);
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------ CTA tier
+
+constexpr int TC_THREADS = 256;
+constexpr int TC_BITMAT_MAXD = 1024;   // roots up to this out-degree keep R in shared memory
+constexpr int TC_HASH_MAXD = 8192;     // beyond this, membership is a binary search in global
+constexpr size_t TC_SMEM = (size_t)2 * 2048 * 4          // hash keys + values (dp <= 1024)
+                           + (size_t)2 * TC_BITMAT_MAXD * 4  // cnt + kc
+                           + (size_t)TC_BITMAT_MAXD * (TC_BITMAT_MAXD / 32) * 4  // R
+                           + (size_t)(TC_THREADS / 32) * 64 * 4;                 // per-warp segments
+// Same budget re-cut for TC_BITMAT_MAXD < dp <= TC_HASH_MAXD: a 16384-slot
+// hash (128 KB) + cnt/kc (64 KB) + segments; checked on the host.
+constexpr size_t TC_SMEM_HASHONLY = (size_t)2 * 16384 * 4 + (size_t)2 * TC_HASH_MAXD * 4 +
+                                    (size_t)(TC_THREADS / 32) * 64 * 4;
+constexpr size_t TC_SMEM_MAX = TC_SMEM > TC_SMEM_HASHONLY ? TC_SMEM : TC_SMEM_HASHONLY;
+
+__device__ __forceinline__ int out_index(const int *hk, const int *hv, unsigned mask, bool use_hash, const int *ncol,
+                                         int s, int e, int w) {
+    if (use_hash) return hset_find(hk, hv, mask, w);
+    int p = find_sorted(ncol, s, e, w);
+    return p < 0 ? -1 : p - s;
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
+                                                        const int *counters) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    constexpr int NW = TC_THREADS / 32;
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    const int nh = counters[CNT_TRI_HEAVY];
+    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int u = heavy[h];
+        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        const bool use_bits = dp <= TC_BITMAT_MAXD;
+        const bool use_hash = dp <= TC_HASH_MAXD;
+        const unsigned H = use_hash ? next_pow2(2 * dp) : 0;
+        const unsigned mask = H ? H - 1 : 0;
+        const int W = (dp + 31) >> 5;  // bit-matrix words per row
+        // carve shared memory
+        // beyond TC_HASH_MAXD the per-position counters live in global memory
+        const int nloc = use_hash ? dp : 0;
+        int *hk = reinterpret_cast<int *>(dsm);
+        int *hv = hk + H;
+        int *cnt = hv + H;
+        int *kc = cnt + nloc;
+        int *segs = kc + nloc;            // NW x 64 ints
+        unsigned *R = reinterpret_cast<unsigned *>(segs + NW * 64);
+        int *sst = segs + wid * 64;
+        int *spre = sst + 32;
+        for (int i = threadIdx.x; i < (int)H; i += TC_THREADS) hk[i] = -1;
+        for (int i = threadIdx.x; i < nloc; i += TC_THREADS) { cnt[i] = 0; kc[i] = 0; }
+        if (use_bits)
+            for (int i = threadIdx.x; i < dp * W; i += TC_THREADS) R[i] = 0;
+        __syncthreads();
+        if (use_hash)
+            for (int i = threadIdx.x; i < dp; i += TC_THREADS) hset_insert(hk, hv, mask, g.ncol[s + i], i);
+        const int umax = g.ncol[e - 1];
+        __syncthreads();
+        long long ku = 0;
+        for (int jb = wid * 32; jb < dp - 1; jb += NW * 32) {
+            const int j = jb + lane;
+            int len = 0, vs = 0;
+            if (j < dp - 1) {
+                const int v = g.ncol[s + j];
+                vs = g.split[v];
+                len = g.nrow[v + 1] - vs;
+            }
+            const int incl = warp_inclusive_scan(len);
+            sst[lane] = vs;
+            spre[lane] = incl - len;
+            const int total = __shfl_sync(FULL, incl, 31);
+            __syncwarp();
+            for (int kb = 0; kb < total; kb += 32) {
+                const int k = kb + lane;
+                if (k >= total) break;
+                const int q = seg_owner(spre, k);
+                const int pos = sst[q] + (k - spre[q]);
+                const int w = g.ncol[pos];
+                if (w > umax) continue;
+                const int i = out_index(hk, hv, mask, use_hash, g.ncol, s, e, w);
+                if (i < 0) continue;
+                const int jj = jb + q;
+                atomicAdd(use_hash ? &cnt[jj] : &tcnt[s + jj], 1);
+                atomicAdd(use_hash ? &cnt[i] : &tcnt[s + i], 1);
+                atomicAdd(&tcnt[pos], 1);
+                if (use_bits) {
+                    atomicOr(&R[jj * W + (i >> 5)], 1u << (i & 31));
+                } else {
+                    // K4 with this triangle (u, v, w): x in N+(w) ∩ N+(u) ∩ N+(v)
+                    const int v = g.ncol[s + jj];
+                    const int vs0 = g.split[v], ve0 = g.nrow[v + 1];
+                    const int ws0 = g.split[w], we0 = g.nrow[w + 1];
+                    for (int p = ws0; p < we0; ++p) {
+                        const int x = g.ncol[p];
+                        if (x > umax) break;
+                        const int ix = out_index(hk, hv, mask, use_hash, g.ncol, s, e, x);
+                        if (ix < 0 || find_sorted(g.ncol, vs0, ve0, x) < 0) continue;
+                        ku += 1;
+                        if (use_hash) {
+                            atomicAdd(&kc[jj], 1);
+                            atomicAdd(&kc[i], 1);
+                            atomicAdd(&kc[ix], 1);
+                        } else {
+                            add64(&vacc[v].K4, 1);
+                            add64(&vacc[w].K4, 1);
+                            add64(&vacc[x].K4, 1);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nloc; i += TC_THREADS)
+            if (cnt[i]) atomicAdd(&tcnt[s + i], cnt[i]);
+        if (use_bits) {
+            for (int j = threadIdx.x; j < dp; j += TC_THREADS) {
+                const unsigned *rj = R + j * W;
+                for (int wd = 0; wd < W; ++wd) {
+                    unsigned bits = rj[wd];
+                    while (bits) {
+                        const int i = wd * 32 + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const unsigned *ri = R + i * W;
+                        int k = 0;
+                        for (int t = (i >> 5); t < W; ++t) {
+                            unsigned x = rj[t] & ri[t];
+                            k += __popc(x);
+                            while (x) { atomicAdd(&kc[t * 32 + __ffs(x) - 1], 1); x &= x - 1; }
+                        }
+                        if (!k) continue;
+                        ku += k;
+                        atomicAdd(&kc[j], k);
+                        atomicAdd(&kc[i], k);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        ku = warp_sum(ku);
+        if (lane == 0 && ku) add64(&vacc[u].K4, ku);
+        for (int i = threadIdx.x; i < nloc; i += TC_THREADS)
+            if (kc[i]) add64(&vacc[g.ncol[s + i]].K4, kc[i]);
+        __syncthreads();
+    }
+}
+
+void launch_stage1(Work &w, cudaStream_t st) {
+    Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
+    k_tri_warp<<<w.num_sms * 8, TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    k_tri_cta<<<w.num_sms * 1, TC_THREADS, TC_SMEM_MAX, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+}
+
+void configure_stage1() {
+    cudaFuncSetAttribute(k_tri_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+}
+
+}  // namespace niorca

@@ -1,0 +1,227 @@
+// stage2.cu -- edge aggregates and the triangle-opposite term, after the
+// per-edge triangle counts t are final.
+//
+// For every out-edge (u, v) with t = t_uv > 0 (edges without a triangle add
+// nothing), both endpoints receive
+//   A1 += t, A2 += t^2, A3 += t * d(other end),
+// the neighbour sums from which the f* variables of Table 1 that involve
+// t_xy follow (f_13^14 = A2 - A1, f_11^13 = (d-1) A1 - A2, ...).
+// Every triangle u < v < w is listed again (as in Stage I) and each corner
+// receives t of the opposite edge minus one:
+//   D12[u] += t_vw - 1, D12[v] += t_uw - 1, D12[w] += t_uv - 1,
+// so that D12(x) = sum over triangles {x,y,z} of (t_yz - 1) = f_12^14
+// (Table 1: the triangles of e_yz other than xyz). Only out-edges with
+// t > 0 are expanded.
+#include "kernels.h"
+
+namespace niorca {
+
+__device__ __forceinline__ int seg_owner2(const int *pre, int k) {
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int AW_MAXD = 64;
+constexpr int AW_WARPS = 8;
+
+struct AggWarpSmem {
+    int hk[2 * AW_MAXD];
+    int hv[2 * AW_MAXD];
+    long long dc[AW_MAXD];
+    int sst[32];
+    int spre[32];
+};
+
+// Edge aggregates of u's out-edges; returns whether any has a triangle.
+__device__ __forceinline__ bool edge_aggregates(const Graph &g, const int *tcnt, VAcc *vacc, int u, int s, int dp,
+                                                int first, int stride) {
+    const int du = g.nrow[u + 1] - g.nrow[u];
+    long long a1 = 0, a2 = 0, a3 = 0;
+    for (int j = first; j < dp; j += stride) {
+        const long long t = tcnt[s + j];
+        if (!t) continue;
+        const int v = g.ncol[s + j];
+        const long long dv = g.nrow[v + 1] - g.nrow[v];
+        a1 += t;
+        a2 += t * t;
+        a3 += t * dv;
+        add64(&vacc[v].A1, t);
+        add64(&vacc[v].A2, t * t);
+        add64(&vacc[v].A3, t * du);
+    }
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    a3 = warp_sum(a3);
+    if (lane_id() == 0 && a1) {
+        add64(&vacc[u].A1, a1);
+        add64(&vacc[u].A2, a2);
+        add64(&vacc[u].A3, a3);
+    }
+    return a1 != 0;
+}
+
+__global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *tcnt, VAcc *vacc, int *heavy,
+                                                            int *counters) {
+    __shared__ AggWarpSmem sm_all[AW_WARPS];
+    AggWarpSmem &S = sm_all[threadIdx.x >> 5];
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int u = gw; u < g.n; u += nw) {
+        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        if (dp < 1) continue;
+        if (dp > AW_MAXD) {
+            if (lane == 0) heavy[atomicAdd(&counters[CNT_AGG_HEAVY], 1)] = u;
+            continue;
+        }
+        if (!edge_aggregates(g, tcnt, vacc, u, s, dp, lane, 32) || dp < 2) continue;
+        const unsigned mask = next_pow2(2 * dp) - 1;
+        for (int i = lane; i <= (int)mask; i += 32) S.hk[i] = -1;
+        for (int i = lane; i < AW_MAXD; i += 32) S.dc[i] = 0;
+        __syncwarp();
+        for (int i = lane; i < dp; i += 32) hset_insert(S.hk, S.hv, mask, g.ncol[s + i], i);
+        const int umax = g.ncol[e - 1];
+        __syncwarp();
+        long long du12 = 0;
+        for (int jb = 0; jb < dp - 1; jb += 32) {
+            const int j = jb + lane;
+            int len = 0, vs = 0;
+            if (j < dp - 1 && tcnt[s + j] > 0) {
+                const int v = g.ncol[s + j];
+                vs = g.split[v];
+                len = g.nrow[v + 1] - vs;
+            }
+            const int incl = warp_inclusive_scan(len);
+            S.sst[lane] = vs;
+            S.spre[lane] = incl - len;
+            const int total = __shfl_sync(FULL, incl, 31);
+            __syncwarp();
+            for (int kb = 0; kb < total; kb += 32) {
+                const int k = kb + lane;
+                if (k >= total) break;
+                const int q = seg_owner2(S.spre, k);
+                const int pos = S.sst[q] + (k - S.spre[q]);
+                const int w = g.ncol[pos];
+                if (w > umax) continue;
+                const int i = hset_find(S.hk, S.hv, mask, w);
+                if (i < 0) continue;
+                const int jj = jb + q;
+                du12 += tcnt[pos] - 1;                                 // t(v, w) - 1 -> u
+                atomicAdd((unsigned long long *)&S.dc[jj], (unsigned long long)(tcnt[s + i] - 1));  // t(u, w) - 1 -> v
+                atomicAdd((unsigned long long *)&S.dc[i], (unsigned long long)(tcnt[s + jj] - 1));  // t(u, v) - 1 -> w
+            }
+            __syncwarp();
+        }
+        du12 = warp_sum(du12);
+        if (lane == 0 && du12) add64(&vacc[u].D12, du12);
+        for (int i = lane; i < dp; i += 32)
+            if (S.dc[i]) add64(&vacc[g.ncol[s + i]].D12, S.dc[i]);
+        __syncwarp();
+    }
+}
+
+constexpr int AC_THREADS = 256;
+constexpr int AC_HASH_MAXD = 8192;
+constexpr size_t AC_SMEM = (size_t)2 * 16384 * 4 + (size_t)AC_HASH_MAXD * 8 + (size_t)(AC_THREADS / 32) * 64 * 4;
+
+__global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
+                                                        const int *counters) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    constexpr int NW = AC_THREADS / 32;
+    __shared__ int any_tri;
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    const int nh = counters[CNT_AGG_HEAVY];
+    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int u = heavy[h];
+        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        if (threadIdx.x == 0) any_tri = 0;
+        __syncthreads();
+        if (edge_aggregates(g, tcnt, vacc, u, s, dp, threadIdx.x, AC_THREADS) && lane == 0) any_tri = 1;
+        __syncthreads();
+        if (!any_tri) continue;
+        const bool use_hash = dp <= AC_HASH_MAXD;
+        const unsigned H = use_hash ? next_pow2(2 * dp) : 0;
+        const unsigned mask = H ? H - 1 : 0;
+        long long *dc = reinterpret_cast<long long *>(dsm);      // dp (only with the hash)
+        int *hk = reinterpret_cast<int *>(dc + (use_hash ? dp : 0));
+        int *hv = hk + H;
+        int *segs = hv + H;
+        int *sst = segs + wid * 64;
+        int *spre = sst + 32;
+        if (use_hash) {
+            for (int i = threadIdx.x; i < (int)H; i += AC_THREADS) hk[i] = -1;
+            for (int i = threadIdx.x; i < dp; i += AC_THREADS) dc[i] = 0;
+        }
+        __syncthreads();
+        if (use_hash)
+            for (int i = threadIdx.x; i < dp; i += AC_THREADS) hset_insert(hk, hv, mask, g.ncol[s + i], i);
+        const int umax = g.ncol[e - 1];
+        __syncthreads();
+        long long du12 = 0;
+        for (int jb = wid * 32; jb < dp - 1; jb += NW * 32) {
+            const int j = jb + lane;
+            int len = 0, vs = 0;
+            if (j < dp - 1 && tcnt[s + j] > 0) {
+                const int v = g.ncol[s + j];
+                vs = g.split[v];
+                len = g.nrow[v + 1] - vs;
+            }
+            const int incl = warp_inclusive_scan(len);
+            sst[lane] = vs;
+            spre[lane] = incl - len;
+            const int total = __shfl_sync(FULL, incl, 31);
+            __syncwarp();
+            for (int kb = 0; kb < total; kb += 32) {
+                const int k = kb + lane;
+                if (k >= total) break;
+                const int q = seg_owner2(spre, k);
+                const int pos = sst[q] + (k - spre[q]);
+                const int w = g.ncol[pos];
+                if (w > umax) continue;
+                int i;
+                if (use_hash) {
+                    i = hset_find(hk, hv, mask, w);
+                } else {
+                    const int p = find_sorted(g.ncol, s, e, w);
+                    i = p < 0 ? -1 : p - s;
+                }
+                if (i < 0) continue;
+                const int jj = jb + q;
+                du12 += tcnt[pos] - 1;
+                const long long tv = tcnt[s + i] - 1, tw = tcnt[s + jj] - 1;
+                if (use_hash) {
+                    atomicAdd((unsigned long long *)&dc[jj], (unsigned long long)tv);
+                    atomicAdd((unsigned long long *)&dc[i], (unsigned long long)tw);
+                } else {
+                    add64(&vacc[g.ncol[s + jj]].D12, tv);
+                    add64(&vacc[w].D12, tw);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+        du12 = warp_sum(du12);
+        if (lane == 0 && du12) add64(&vacc[u].D12, du12);
+        if (use_hash)
+            for (int i = threadIdx.x; i < dp; i += AC_THREADS)
+                if (dc[i]) add64(&vacc[g.ncol[s + i]].D12, dc[i]);
+        __syncthreads();
+    }
+}
+
+void launch_stage2(Work &w, cudaStream_t st) {
+    Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
+    int *heavy = w.lists + (size_t)w.n;
+    k_agg_warp<<<w.num_sms * 8, AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    k_agg_cta<<<w.num_sms, AC_THREADS, AC_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+}
+
+void configure_stage2() {
+    cudaFuncSetAttribute(k_agg_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AC_SMEM);
+}
+
+}  // namespace niorca

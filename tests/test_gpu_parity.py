@@ -1,0 +1,177 @@
+"""CUDA path vs the oracle, element by element (integers: bit-exact).
+
+Every call goes through the C ABI (paper_2606_29651_gb300 is a ctypes
+binding of libniorca.so)."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from helpers import (cheap_sum_checks, closed_complete, closed_complete_bipartite, closed_cycle, closed_path,
+                     closed_star, random_small_graphs)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ni():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2606_29651_gb300 as ni
+    ni.build()
+    return ni
+
+
+def gpu_count(ni, rp, ci):
+    dev = torch.device("cuda:0")
+    r = torch.from_numpy(np.ascontiguousarray(rp, dtype=np.int32)).to(dev)
+    c = torch.from_numpy(np.ascontiguousarray(ci, dtype=np.int32)).to(dev)
+    out = ni.count(r, c)
+    ni.check()
+    return out.cpu().numpy()
+
+
+def assert_same(got, exp, what):
+    if not np.array_equal(got, exp):
+        bad = np.argwhere(got != exp)
+        v, k = bad[0]
+        raise AssertionError(f"{what}: {len(bad)} mismatches; first vertex {v} orbit {k}: "
+                             f"got {got[v, k]} expected {exp[v, k]}; row got {got[v].tolist()} exp {exp[v].tolist()}")
+
+
+def test_tiny_random_graphs_vs_brute_force(ni):
+    for n, edges in random_small_graphs(120, 10, seed=101):
+        rp, ci = gg.from_edges(n, edges) if edges else (np.zeros(n + 1, np.int32), np.zeros(0, np.int32))
+        exp = np.array(oracle.brute_count(n, edges), dtype=np.int64).reshape(n, 15)
+        assert_same(gpu_count(ni, rp, ci), exp, f"n={n} edges={edges}")
+
+
+def test_closed_forms(ni):
+    for n in (2, 3, 4, 5, 12, 40, 100, 300):
+        assert_same(gpu_count(ni, *gg.complete(n)), np.tile(np.array(closed_complete(n)), (n, 1)), f"K{n}")
+    for k in (1, 2, 3, 50, 3000):
+        assert_same(gpu_count(ni, *gg.star(k)), closed_star(k), f"star{k}")
+    for n in (3, 4, 5, 1000):
+        assert_same(gpu_count(ni, *gg.cycle(n)), closed_cycle(n), f"C{n}")
+    for n in (2, 5, 777):
+        assert_same(gpu_count(ni, *gg.path(n)), closed_path(n), f"P{n}")
+    for a, b in ((1, 1), (3, 7), (40, 60), (2, 12000), (3, 9000)):
+        assert_same(gpu_count(ni, *gg.complete_bipartite(a, b)), closed_complete_bipartite(a, b), f"K{a},{b}")
+
+
+def test_complete_graph_beyond_bitmatrix(ni):
+    # out-degrees above 1024 take the probing K4 path
+    n = 1040
+    assert_same(gpu_count(ni, *gg.complete(n)), np.tile(np.array(closed_complete(n)), (n, 1)), f"K{n}")
+
+
+def test_empty_and_edgeless(ni):
+    rp = np.zeros(6, np.int32)
+    assert_same(gpu_count(ni, rp, np.zeros(0, np.int32)), np.zeros((5, 15), np.int64), "edgeless")
+    out = ni.count(torch.zeros(1, dtype=torch.int32, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"))
+    assert out.shape == (0, 15)
+
+
+def test_er2000_full_vs_oracle_and_definition(ni):
+    rp, ci = gg.er(2000, 0.01, 1)
+    got = gpu_count(ni, rp, ci)
+    assert_same(got, oracle.count(rp, ci), "ER2000 vs three-stage oracle")
+    assert_same(got, oracle.definition_count(rp, ci), "ER2000 vs definition")
+
+
+@pytest.mark.parametrize("name,make", [
+    ("rmat12", lambda: gg.rmat(12, 16, seed=3)),
+    ("rmat14", lambda: gg.rmat(14, 16, seed=4)),
+    ("chunglu20k", lambda: gg.chunglu(20000, 2.2, 12.0, 5)),
+    ("er_dense", lambda: gg.er(600, 0.5, 6)),
+    ("er_sparse", lambda: gg.er_mean_degree(50000, 6, 7)),
+])
+def test_medium_graphs_full_vs_oracle(ni, name, make):
+    rp, ci = make()
+    assert_same(gpu_count(ni, rp, ci), oracle.count(rp, ci), name)
+
+
+def test_repeated_calls_identical(ni):
+    rp, ci = gg.rmat(13, 16, seed=8)
+    a = gpu_count(ni, rp, ci)
+    for _ in range(3):
+        assert np.array_equal(gpu_count(ni, rp, ci), a)
+
+
+def _full_size_check(ni, rp, ci, nsample, seed):
+    """Invariants over all rows, then oracle rows for a sample: random
+    vertices, the 40 largest vertices of degree <= 5000 (their pair loops
+    stay affordable for the oracle) and 40 neighbours of the largest hub."""
+    got = gpu_count(ni, rp, ci)
+    assert cheap_sum_checks(rp, got) == []
+    d = np.diff(rp)
+    rng = np.random.default_rng(seed)
+    pick = set(rng.choice(len(d), size=nsample, replace=False).tolist())
+    order = np.argsort(-d, kind="stable")
+    pick.update(int(v) for v in order[d[order] <= 5000][:40])
+    top = int(order[0])
+    nb = ci[rp[top]:rp[top + 1]]
+    pick.update(int(v) for v in rng.choice(nb, size=min(40, len(nb)), replace=False))
+    verts = np.array(sorted(pick), dtype=np.int32)
+    exp = oracle.count_vertices(rp, ci, verts)
+    assert_same(got[verts], exp, "sampled rows")
+    return got
+
+
+def test_er_1e6_sampled(ni):
+    rp, ci = gg.er_mean_degree(1_000_000, 32, 1)
+    _full_size_check(ni, rp, ci, 300, 11)
+
+
+def test_rmat22_sampled(ni):
+    rp, ci = gg.rmat(22, 16, seed=1)
+    _full_size_check(ni, rp, ci, 200, 12)
+
+
+def test_batch_equals_single(ni):
+    graphs = [gg.chunglu(int(n), 2.5, 8.0, 100 + i) for i, n in enumerate([50, 3, 1, 700, 2500, 90, 1200])]
+    graphs.append(gg.complete(30))
+    graphs.append((np.zeros(4, np.int32), np.zeros(0, np.int32)))   # edgeless graph of 3 vertices
+    rowptr, colidx, vo, eo = gg.pack(graphs)
+    dev = torch.device("cuda:0")
+    out = ni.count_batch(torch.from_numpy(rowptr.astype(np.int32)).to(dev), torch.from_numpy(colidx).to(dev),
+                         torch.from_numpy(vo).to(dev), torch.from_numpy(eo).to(dev))
+    ni.check()
+    got = out.cpu().numpy()
+    for g, (rp, ci) in enumerate(graphs):
+        rows = got[vo[g]:vo[g + 1]]
+        assert_same(rows, oracle.count(rp, ci), f"graph {g} in batch")
+        assert_same(rows, gpu_count(ni, rp, ci), f"graph {g} batch vs alone")
+
+
+def _expect_status(ni, rp, ci, status):
+    dev = torch.device("cuda:0")
+    ni.last_status()   # clear
+    ni.count(torch.as_tensor(rp, dtype=torch.int32, device=dev), torch.as_tensor(ci, dtype=torch.int32, device=dev))
+    assert ni.last_status() == status
+
+
+def test_device_detected_errors(ni):
+    from paper_2606_29651_gb300 import Status
+    # rowptr[n] != m, out-of-range column, self-loop, unsorted row
+    _expect_status(ni, [0, 1, 2], [1, 0, 0], Status.EINVAL)
+    _expect_status(ni, [0, 1, 2], [7, 0], Status.EINVAL)
+    _expect_status(ni, [0, 2, 3], [0, 1, 0], Status.ENOTSIMPLE)
+    _expect_status(ni, [0, 2, 3, 4], [2, 1, 0, 0], Status.ENOTSIMPLE)
+    # a clean graph after errors reports OK again
+    _expect_status(ni, *gg.complete(5), Status.OK)
+
+
+def test_validate_detects_asymmetry(ni):
+    from paper_2606_29651_gb300 import Status
+    dev = torch.device("cuda:0")
+    ni.last_status()
+    rp = torch.tensor([0, 1, 1], dtype=torch.int32, device=dev)     # 0 -> 1 without 1 -> 0
+    ci = torch.tensor([1], dtype=torch.int32, device=dev)
+    ni.validate(rp, ci)
+    assert ni.last_status() == Status.ENOTSIMPLE
+    rp2, ci2 = gg.rmat(10, 8, seed=1)
+    ni.validate(torch.from_numpy(rp2).to(dev), torch.from_numpy(ci2).to(dev))
+    assert ni.last_status() == Status.OK
