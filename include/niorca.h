@@ -122,6 +122,28 @@ const char *niorca_status_string(niorca_status s);
 /* Library version, major * 10000 + minor * 100 + patch. */
 int32_t niorca_version(void);
 
+/*
+ * Tracing (no counterpart in the paper, which reports PAPI counters; here
+ * CUDA events). When enabled, every kernel the library launches is followed
+ * by an event on the call's stream, so the time of each kernel is the gap
+ * between consecutive events. Keep it off while capturing a CUDA graph.
+ *   niorca_profile_enable  switch per-kernel timing on (1) or off (0).
+ *   niorca_profile_read    waits for the recorded events, then writes the
+ *                          accumulated milliseconds and launch counts of
+ *                          every kernel id (0 .. return value - 1) into
+ *                          ms[] and launches[] (either may be NULL; at most
+ *                          max_kernels entries). Returns the number of ids.
+ *   niorca_profile_reset   clears the totals.
+ *   niorca_kernel_name     name of a kernel id (static string).
+ *   niorca_launch_count    kernels launched by the library since it was
+ *                          loaded, timing on or off.
+ */
+void niorca_profile_enable(int32_t on);
+int32_t niorca_profile_read(double *ms, int64_t *launches, int32_t max_kernels);
+void niorca_profile_reset(void);
+const char *niorca_kernel_name(int32_t id);
+int64_t niorca_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,6 +58,16 @@ def _lib():
     h.niorca_status_string.argtypes = [ctypes.c_int]
     h.niorca_version.restype = i32
     h.niorca_version.argtypes = []
+    h.niorca_profile_enable.restype = None
+    h.niorca_profile_enable.argtypes = [i32]
+    h.niorca_profile_read.restype = i32
+    h.niorca_profile_read.argtypes = [vp, vp, i32]
+    h.niorca_profile_reset.restype = None
+    h.niorca_profile_reset.argtypes = []
+    h.niorca_kernel_name.restype = ctypes.c_char_p
+    h.niorca_kernel_name.argtypes = [i32]
+    h.niorca_launch_count.restype = i64
+    h.niorca_launch_count.argtypes = []
     _handle = h
     return h
 
@@ -157,3 +167,27 @@ def batch_workspace_bytes(num_graphs: int, total_n: int, total_m: int) -> int:
 
 def version() -> int:
     return int(_lib().niorca_version())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Per-kernel CUDA-event timing on the launching stream (see niorca.h)."""
+    _lib().niorca_profile_enable(1 if on else 0)
+
+
+def profile_reset() -> None:
+    _lib().niorca_profile_reset()
+
+
+def profile_read() -> dict:
+    """{kernel name: (total ms, launches)} accumulated since the last reset."""
+    import numpy as np
+    k = 64
+    ms = np.zeros(k, dtype=np.float64)
+    cnt = np.zeros(k, dtype=np.int64)
+    nk = _lib().niorca_profile_read(ms.ctypes.data, cnt.ctypes.data, k)
+    return {_lib().niorca_kernel_name(i).decode(): (float(ms[i]), int(cnt[i])) for i in range(nk)}
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(_lib().niorca_launch_count())

@@ -253,10 +253,14 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
 void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
     k_c4_warp<<<w.num_sms * 16, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters);
+    after_launch(st, K_C4_WARP);
     k_c4_cta<<<w.num_sms * 2, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters);
+    after_launch(st, K_C4_CTA);
     if (w.c4slots > 0) {
         k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, w.n, w.c4slots, w.counters);
+        after_launch(st, K_C4_ZERO);
         k_c4_global<<<w.c4slots, CG_THREADS, 0, st>>>(g, w.vacc, w.lists, w.counters, w.c4dense, w.c4slots);
+        after_launch(st, K_C4_GLOBAL);
     }
 }
 

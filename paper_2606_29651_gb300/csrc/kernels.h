@@ -48,7 +48,16 @@ void launch_solve(Work &w, long long *out, cudaStream_t st);
 void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *status, int num_sms,
                      cudaStream_t st);
 
-// Opt-in to large dynamic shared memory for every kernel that needs it.
-void configure_kernels();
+// Kernel ids for the optional per-kernel event timing and launch counting.
+enum KernelId {
+    K_CLASS_HIST, K_SCAN, K_CLASS_SCATTER, K_RELABEL_WARP, K_RELABEL_CTA, K_BATCH_SETUP,
+    K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_ZERO, K_C4_GLOBAL,
+    K_SOLVE, K_VALIDATE, K_COUNT
+};
+const char *kernel_name(int id);
+
+// Called after every kernel launch: counts it and, when timing is on,
+// records an event on the launching stream.
+void after_launch(cudaStream_t st, int id);
 
 }  // namespace niorca

@@ -1,8 +1,11 @@
 // niorca_api.cu -- the C ABI (include/niorca.h): argument checks, per-device
 // state, work memory and the launch sequence of the three stages.
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "../../include/niorca.h"
 #include "kernels.h"
@@ -16,7 +19,77 @@ void launch_batch_setup(const int *rowptr, const long long *vtx_offset, const lo
                         int total_n, int2 *vrange, int *status, int num_sms, cudaStream_t st);
 void launch_relabel_batch(const int *rowptr, const int *colidx, const int2 *vrange, Work &w, cudaStream_t st);
 
+// ------------------------------------------------ launch counting and timing
+
 namespace {
+std::atomic<long long> g_launches{0};
+std::atomic<int> g_prof_on{0};
+struct Timeline {
+    cudaEvent_t start = nullptr;
+    std::vector<std::pair<cudaEvent_t, int>> marks;  // event after each kernel
+};
+std::mutex g_prof_mu;
+std::vector<Timeline> g_pending;
+double g_ms[K_COUNT];
+long long g_calls[K_COUNT];
+thread_local Timeline *t_cur = nullptr;
+
+const char *const kNames[K_COUNT] = {
+    "k_class_hist", "k_scan", "k_class_scatter", "k_relabel_rows_warp", "k_relabel_rows_cta", "k_batch_setup",
+    "k_tri_warp", "k_tri_cta", "k_agg_warp", "k_agg_cta", "k_c4_warp", "k_c4_cta", "k_c4_zero_dense",
+    "k_c4_global", "k_solve", "k_validate"};
+}  // namespace
+
+const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
+
+void after_launch(cudaStream_t st, int id) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (t_cur) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) == cudaSuccess) {
+            cudaEventRecord(e, st);
+            t_cur->marks.emplace_back(e, id);
+        }
+    }
+}
+
+namespace {
+
+// Starts the event timeline of one call (when timing is on).
+void timeline_begin(cudaStream_t st) {
+    if (!g_prof_on.load()) return;
+    t_cur = new Timeline();
+    if (cudaEventCreate(&t_cur->start) == cudaSuccess) cudaEventRecord(t_cur->start, st);
+}
+
+void timeline_end() {
+    if (!t_cur) return;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        g_pending.push_back(std::move(*t_cur));
+    }
+    delete t_cur;
+    t_cur = nullptr;
+}
+
+// Waits for every recorded timeline and folds it into the totals.
+void timeline_collect() {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (Timeline &t : g_pending) {
+        cudaEvent_t prev = t.start;
+        for (auto &mk : t.marks) {
+            float ms = 0.f;
+            if (prev && cudaEventSynchronize(mk.first) == cudaSuccess && cudaEventElapsedTime(&ms, prev, mk.first) == cudaSuccess) {
+                g_ms[mk.second] += ms;
+                g_calls[mk.second] += 1;
+            }
+            prev = mk.first;
+        }
+        if (t.start) cudaEventDestroy(t.start);
+        for (auto &mk : t.marks) cudaEventDestroy(mk.first);
+    }
+    g_pending.clear();
+}
 
 struct DeviceState {
     bool ready = false;
@@ -131,6 +204,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     w.status = ds->status;
     w.num_sms = ds->num_sms;
     cudaMemsetAsync(w.counters, 0, 4 * 16, st);
+    timeline_begin(st);
     if (batch) {
         int2 *vrange = reinterpret_cast<int2 *>(b + L.vrange);
         launch_batch_setup(rowptr, vtx_offset, edge_offset, num_graphs, n, vrange, ds->status, ds->num_sms, st);
@@ -142,6 +216,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     launch_stage2(w, st);
     launch_cycle4(w, st);
     launch_solve(w, out, st);
+    timeline_end();
     s = check_launch();
     cudaFreeAsync(base, st);
     return s;
@@ -229,3 +304,25 @@ extern "C" const char *niorca_status_string(niorca_status s) {
 }
 
 extern "C" int32_t niorca_version(void) { return 100; }
+
+extern "C" void niorca_profile_enable(int32_t on) { g_prof_on.store(on ? 1 : 0); }
+
+extern "C" int32_t niorca_profile_read(double *ms, int64_t *launches, int32_t max_kernels) {
+    timeline_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int i = 0; i < K_COUNT && i < max_kernels; ++i) {
+        if (ms) ms[i] = g_ms[i];
+        if (launches) launches[i] = g_calls[i];
+    }
+    return K_COUNT;
+}
+
+extern "C" void niorca_profile_reset(void) {
+    timeline_collect();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (int i = 0; i < K_COUNT; ++i) { g_ms[i] = 0; g_calls[i] = 0; }
+}
+
+extern "C" const char *niorca_kernel_name(int32_t id) { return kernel_name(id); }
+
+extern "C" int64_t niorca_launch_count(void) { return g_launches.load(); }

@@ -108,8 +108,11 @@ void launch_exclusive_scan(const int *in, int *out, long long len, bool write_to
         return;
     }
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, len, part);
+    after_launch(st, K_SCAN);
     k_scan_top<<<1, 1024, 0, st>>>(part, nb);
+    after_launch(st, K_SCAN);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, out, len, part, write_total ? 1 : 0);
+    after_launch(st, K_SCAN);
 }
 
 // ------------------------------------------------------------- class order
@@ -387,15 +390,19 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
 static void relabel_common(const int *rowptr, const int *colidx, const int2 *vrange, Work &w, cudaStream_t st) {
     const int nt = w.ntiles;
     k_class_hist<<<nt, RL_THREADS, 0, st>>>(rowptr, w.n, w.m, w.vinfo, w.chist, nt, w.counters, w.status);
+    after_launch(st, K_CLASS_HIST);
     launch_exclusive_scan(w.chist, w.coff, (long long)NCLASS * nt, false, w.scan_part, st);
     // ndeg (degree of each new id) is staged in `split`, then scanned into nrow
     k_class_scatter<<<nt, RL_THREADS, 0, st>>>(w.n, w.vinfo, w.coff, nt, w.perm, w.split);
+    after_launch(st, K_CLASS_SCATTER);
     launch_exclusive_scan(w.split, w.nrow, w.n, true, w.scan_part, st);
     k_relabel_rows_warp<<<w.num_sms * 8, 256, 0, st>>>(rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow, w.coff,
                                                        nt, w.ncol, w.split, w.vacc, w.tcnt, w.status);
+    after_launch(st, K_RELABEL_WARP);
     k_relabel_rows_cta<<<w.num_sms * 2, RLC_THREADS, 0, st>>>(rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow,
                                                               w.coff, nt, w.ncol, w.split, w.vacc, w.tcnt,
                                                               w.status);
+    after_launch(st, K_RELABEL_CTA);
 }
 
 void launch_relabel(const int *rowptr, const int *colidx, Work &w, cudaStream_t st) {
@@ -435,6 +442,7 @@ __global__ void k_batch_setup(const int *rowptr, const long long *vo, const long
 void launch_batch_setup(const int *rowptr, const long long *vtx_offset, const long long *edge_offset, int num_graphs,
                         int total_n, int2 *vrange, int *status, int num_sms, cudaStream_t st) {
     k_batch_setup<<<num_sms * 4, 256, 0, st>>>(rowptr, vtx_offset, edge_offset, num_graphs, total_n, vrange, status);
+    after_launch(st, K_BATCH_SETUP);
 }
 
 }  // namespace niorca

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
     k_solve<<<w.num_sms * 8, 256, 0, st>>>(g, w.vacc, w.perm, out);
+    after_launch(st, K_SOLVE);
 }
 
 // Full simple-graph check: offsets, strictly increasing rows, no self-loops,
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(256) k_validate(const int *rowptr, const int *
 void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *status, int num_sms, cudaStream_t st) {
     if (n <= 0) return;
     k_validate<<<num_sms * 8, 256, 0, st>>>(rowptr, colidx, n, m, status);
+    after_launch(st, K_VALIDATE);
 }
 
 }  // namespace niorca

@@ -281,7 +281,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
 void launch_stage1(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
     k_tri_warp<<<w.num_sms * 8, TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    after_launch(st, K_TRI_WARP);
     k_tri_cta<<<w.num_sms * 1, TC_THREADS, TC_SMEM_MAX, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    after_launch(st, K_TRI_CTA);
 }
 
 void configure_stage1() {

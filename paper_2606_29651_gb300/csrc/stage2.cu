@@ -217,7 +217,9 @@ void launch_stage2(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
     int *heavy = w.lists + (size_t)w.n;
     k_agg_warp<<<w.num_sms * 8, AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    after_launch(st, K_AGG_WARP);
     k_agg_cta<<<w.num_sms, AC_THREADS, AC_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    after_launch(st, K_AGG_CTA);
 }
 
 void configure_stage2() {

@@ -1,0 +1,79 @@
+"""bench.py pieces that run without a GPU: the reference (oracle) arm, the
+algorithmic byte counts, and the max-over-ranks timing reduction of the
+multi-GPU (replica) path, exercised with gloo ranks on the CPU."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import graphgen as gg  # noqa: E402
+
+
+def test_reference_arm_prints_one_json_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert out.returncode == 0, out.stderr
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference"
+    assert rec["metric"] == bench.METRIC and rec["unit"] == "edges/s"
+    assert rec["value"] > 0 and rec["cpu_baseline"]["kind"] == "oracle"
+    assert rec["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_algorithmic_bytes_small_cases():
+    # a triangle: one oriented edge pair closes it; no 4-cycle wedge pair
+    rp, ci = gg.complete(3)
+    ab = bench.algorithmic_bytes(rp, ci)
+    assert ab["B_csr"] == 4 * 4 + 4 * 6
+    assert ab["B_out"] == 360
+    # the 4-cycle 0-1-2-3: root 3 has wedges 3-0-1 and 3-2-1, root 2 has 2-1-0
+    ab = bench.algorithmic_bytes(*gg.cycle(4))
+    assert ab["W_c4"] == 3
+
+
+def test_deg_class_matches_library_rule():
+    d = np.array([0, 1, 7, 8, 9, 10, 12, 15, 16, 20, 1 << 20, (1 << 20) + (1 << 19)])
+    c = bench.deg_class(d)
+    assert c.tolist()[:3] == [0, 1, 7]
+    assert c[3] == 8 and c[4] == 8 and c[5] == 9 and c[6] == 10 and c[7] == 11 and c[8] == 12
+    assert (np.diff(bench.deg_class(np.arange(0, 5000))) >= 0).all()
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    q.put((rank, bench.reduce_max(1.0 + rank * 2.5, world)))
+    dist.destroy_process_group()
+
+
+def test_reduce_max_over_gloo_ranks():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+    assert all(v == pytest.approx(3.5) for _, v in res)
