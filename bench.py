@@ -328,6 +328,170 @@ def run_ours(args) -> None:
         torch.distributed.destroy_process_group()
 
 
+def run_single_config(args) -> None:
+    """Other single-graph configurations (not the headline): ER2000, RMAT22."""
+    import torch
+
+    import graphgen as gg
+    import paper_2606_29651_gb300 as ni
+    dev = torch.device("cuda", 0)
+    ni.build()
+    if args.workload == "er2000":
+        rp, ci = gg.er(2000, 0.01, 1)
+        desc = "Erdos-Renyi G(n=2000, p=0.01), seed 1"
+    else:
+        rp, ci = gg.rmat(22, 16, seed=1)
+        desc = "R-MAT scale 22, edge factor 16, (.57,.19,.19,.05), seed 1"
+    edges = len(ci) // 2
+    d_rp, d_ci = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    out = torch.empty((len(rp) - 1, 15), dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        ni.count(d_rp, d_ci, out)
+    torch.cuda.synchronize()
+    ni.check()
+    ni.profile_reset()
+    ni.profile_enable(True)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        ni.count(d_rp, d_ci, out)
+    e.record()
+    torch.cuda.synchronize()
+    ni.profile_enable(False)
+    ms = s.elapsed_time(e) / args.steps
+    prof = {k: round(v[0] / v[1], 4) for k, v in ni.profile_read().items() if v[1]}
+    # latency of one call without timing events (launch-bound at this size)
+    ni.check()
+    print(json.dumps({"workload": desc, "edges": edges, "ms_per_call": ms, "edges_per_s": edges / (ms * 1e-3),
+                      "kernel_ms": prof}), flush=True)
+
+
+def run_batch(args) -> None:
+    """Config 4: 8192 Chung-Lu graphs, one batched call; captured CUDA graph
+    replay; against one niorca_count launch sequence per graph."""
+    import torch
+
+    import graphgen as gg
+    import paper_2606_29651_gb300 as ni
+    dev = torch.device("cuda", 0)
+    ni.build()
+    count = args.batch_graphs
+    graphs = gg.chunglu_batch(count, 2.5, 8.0, 50, 5000, seed=1)
+    rowptr, colidx, vo, eo = gg.pack(graphs)
+    d_rp = torch.from_numpy(rowptr.astype(np.int32)).to(dev)
+    d_ci = torch.from_numpy(colidx).to(dev)
+    d_vo, d_eo = torch.from_numpy(vo).to(dev), torch.from_numpy(eo).to(dev)
+    out = torch.empty((len(rowptr) - 1, 15), dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        ni.count_batch(d_rp, d_ci, d_vo, d_eo, out)
+    torch.cuda.synchronize()
+    ni.check()
+    ref = out.clone()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(args.steps):
+        ni.count_batch(d_rp, d_ci, d_vo, d_eo, out)
+    e.record()
+    torch.cuda.synchronize()
+    ms_eager = s.elapsed_time(e) / args.steps
+    # captured once, replayed
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ni.count_batch(d_rp, d_ci, d_vo, d_eo, out)
+    g.replay()
+    torch.cuda.synchronize()
+    s.record()
+    for _ in range(args.steps):
+        g.replay()
+    e.record()
+    torch.cuda.synchronize()
+    ms_graph = s.elapsed_time(e) / args.steps
+    same = bool(torch.equal(out, ref))
+    # one graph per launch sequence, same GPU, graphs already resident
+    singles = [(torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev),
+                torch.empty((len(r) - 1, 15), dtype=torch.int64, device=dev)) for r, c in graphs]
+    for r, c, o in singles[:64]:
+        ni.count(r, c, o)
+    torch.cuda.synchronize()
+    s.record()
+    for r, c, o in singles:
+        ni.count(r, c, o)
+    e.record()
+    torch.cuda.synchronize()
+    ms_single = s.elapsed_time(e)
+    ni.check()
+    print(json.dumps({
+        "workload": f"batched: {count} Chung-Lu graphs, gamma 2.5, n log-uniform [50, 5000], mean degree 8",
+        "graphs": count, "vertices": int(vo[-1]), "edges": int(eo[-1] // 2),
+        "graphs_per_s_batched": count / (ms_eager * 1e-3), "graphs_per_s_cuda_graph": count / (ms_graph * 1e-3),
+        "graphs_per_s_one_per_launch": count / (ms_single * 1e-3), "ms_batched": ms_eager,
+        "ms_cuda_graph": ms_graph, "ms_one_per_launch": ms_single, "replay_bit_exact": same}), flush=True)
+
+
+def run_serve(args) -> None:
+    """Config 5: Poisson arrivals of ER / Chung-Lu graphs, continuous batching."""
+    import graphgen as gg
+    import paper_2606_29651_gb300 as ni
+    from paper_2606_29651_gb300.serve import Server, latency_stats
+    ni.build()
+    nreq = args.serve_requests
+    u = gg.uniform(1, 11, 4 * nreq)
+    graphs = []
+    for i in range(nreq):
+        e = float(np.exp(np.log(1e3) + u[i] * (np.log(args.serve_max_edges) - np.log(1e3))))
+        dmean = 4 + 28 * u[nreq + i]
+        n = max(int(2 * e / dmean), 8)
+        if u[2 * nreq + i] < 0.5:
+            graphs.append(gg.er_mean_degree(n, dmean, 100 + i))
+        else:
+            graphs.append(gg.chunglu(n, 2.2 + 0.8 * u[3 * nreq + i], dmean, 100 + i))
+    total_edges = sum(len(c) // 2 for _, c in graphs)
+    budget = args.serve_budget_gb << 30
+    with Server(0, mem_budget=budget) as srv:          # capacity: everything submitted at once
+        for rp, ci in graphs[:8]:
+            srv.submit(rp, ci).result()
+        t0 = time.perf_counter()
+        futs = [srv.submit(rp, ci) for rp, ci in graphs]
+        for f in futs:
+            f.result()
+        cap = nreq / (time.perf_counter() - t0)
+    by_load = {}
+    for rho in (0.5, 0.8, 0.95):
+        lam = rho * cap
+        gaps = -np.log(1.0 - gg.uniform(2, int(rho * 100), nreq)) / lam
+        with Server(0, mem_budget=budget) as srv:
+            futs = []
+            t0 = time.perf_counter()
+            t_next = t0
+            for i, (rp, ci) in enumerate(graphs):
+                t_next += gaps[i]
+                while time.perf_counter() < t_next:
+                    time.sleep(0)
+                futs.append(srv.submit(rp, ci))
+            for f in futs:
+                f.result()
+            span = time.perf_counter() - t0
+            batches = srv.batches
+        lat = [f.request.t_done - f.request.t_submit for f in futs]
+        by_load[str(rho)] = dict(graphs_per_s=nreq / span, edges_per_s=total_edges / span, batches=batches,
+                                 **latency_stats(lat))
+    # the same requests one call at a time, no batching
+    import torch
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    for rp, ci in graphs:
+        o = ni.count(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
+        o.cpu()
+    one_by_one = nreq / (time.perf_counter() - t0)
+    print(json.dumps({"workload": f"served: {nreq} Poisson requests, ER / Chung-Lu (gamma 2.2-3.0), "
+                                  f"|E| log-uniform [1e3, {args.serve_max_edges:.0e}]",
+                      "total_edges": total_edges, "capacity_graphs_per_s": cap,
+                      "one_call_per_request_graphs_per_s": one_by_one, "by_load": by_load}), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,13 +499,25 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["er1e6", "er2000", "rmat22", "batch", "serve"], default="er1e6",
+                    help="er1e6 is the headline line; the others print their own records")
+    ap.add_argument("--batch-graphs", type=int, default=8192)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-max-edges", type=float, default=5e6)
+    ap.add_argument("--serve-budget-gb", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "er1e6":
         run_ours(args)
+    elif args.workload in ("er2000", "rmat22"):
+        run_single_config(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    else:
+        run_serve(args)
 
 
 if __name__ == "__main__":

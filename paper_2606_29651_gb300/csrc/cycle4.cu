@@ -18,7 +18,7 @@
 
 namespace niorca {
 
-constexpr int CW_WARPS = 4;   // 4 x 8.7 KB of static shared memory
+constexpr int CW_WARPS = 4;   // 4 x 11 KB of static shared memory
 constexpr int CW_SLOTS = 1024;
 constexpr int CW_MAXW = CW_SLOTS / 2;
 constexpr int CC_THREADS = 512;
@@ -46,10 +46,11 @@ __device__ __forceinline__ int wedge_cut(const Graph &g, int v, int u) {
 // Walks the wedges of root u: for every chunk of 32 in-neighbours (starting
 // at chunk `c0`, step `cstep` chunks), sets up the segment table of the warp
 // and calls f(q, pos) for each wedge (q: lane that owns v, pos: position of w),
-// then done(q_lane_v, seg_len) once per chunk after a __syncwarp.
+// then done(v, seg_len) once per chunk after a __syncwarp. `lens`, when not
+// null, holds the segment length of the first `nlens` in-neighbours.
 template <class F, class D>
 __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep, int *sst,
-                                            int *spre, F f, D done) {
+                                            int *spre, F f, D done, const int *lens = nullptr, int nlens = 0) {
     const int lane = lane_id();
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
         const int p = cb + lane;
@@ -57,7 +58,7 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
         if (p < din) {
             v = g.ncol[b + p];
             st = g.nrow[v];
-            len = wedge_cut(g, v, u) - st;
+            len = p < nlens ? lens[p] : wedge_cut(g, v, u) - st;
         }
         const int incl = warp_inclusive_scan(len);
         sst[lane] = st;
@@ -76,14 +77,37 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
     }
 }
 
+constexpr int CW_LENS = 64;   // cached wedge-segment lengths per root
+
 struct C4WarpSmem {
-    int hk[CW_SLOTS];
-    int hc[CW_SLOTS];
+    int hk[CW_SLOTS];      // keys (-1 = empty); all empty between roots
+    int hc[CW_SLOTS];      // wedge counts per key
+    int touched[CW_MAXW];  // slots filled by the current root
+    int lens[CW_LENS];
     int sst[32];
     int spre[32];
     long long pv[32];
+    int ntouched;
 };
 
+// Counts `key`; returns the slot when this call inserted it, else -1.
+__device__ __forceinline__ int hcount_add_new(int *keys, int *cnts, unsigned mask, int key) {
+    unsigned s = hash_slot(key, mask);
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        int k = keys[s];
+        if (k == -1) {
+            const int prev = atomicCAS(&keys[s], -1, key);
+            if (prev == -1) { atomicAdd(&cnts[s], 1); return (int)s; }
+            k = prev;
+        }
+        if (k == key) { atomicAdd(&cnts[s], 1); return -1; }
+        s = (s + 1) & mask;
+    }
+    return -1;
+}
+
+// One warp per root with at most CW_MAXW wedges. The table is cleared once
+// per warp; afterwards every root empties only the slots it filled.
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
@@ -92,13 +116,19 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     int *cta_list = lists + 2 * (size_t)g.n;
     int *glob_list = lists + 3 * (size_t)g.n;
+    constexpr unsigned mask = CW_SLOTS - 1;
+    for (int i = lane; i < CW_SLOTS; i += 32) { S.hk[i] = -1; S.hc[i] = 0; }
+    if (lane == 0) S.ntouched = 0;
+    __syncwarp();
     for (int u = gw; u < g.n; u += nw) {
         const int b = g.nrow[u], din = g.split[u] - b;
         if (din < 2) continue;
         long long W = 0;
         for (int p = lane; p < din; p += 32) {
             const int v = g.ncol[b + p];
-            W += wedge_cut(g, v, u) - g.nrow[v];
+            const int len = wedge_cut(g, v, u) - g.nrow[v];
+            if (p < CW_LENS) S.lens[p] = len;
+            W += len;
         }
         W = warp_sum(W);
         if (W < 2) continue;
@@ -109,35 +139,50 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             }
             continue;
         }
-        const unsigned mask = next_pow2((unsigned)(2 * W)) - 1;
-        for (int i = lane; i <= (int)mask; i += 32) { S.hk[i] = -1; S.hc[i] = 0; }
         __syncwarp();
-        walk_wedges(g, u, b, din, 0, 1, S.sst, S.spre,
-                    [&](int, int pos) { hcount_add(S.hk, S.hc, mask, g.ncol[pos]); },
-                    [&](int, int) {});
+        walk_wedges(
+            g, u, b, din, 0, 1, S.sst, S.spre,
+            [&](int, int pos) {
+                const int slot = hcount_add_new(S.hk, S.hc, mask, g.ncol[pos]);
+                if (slot >= 0) S.touched[atomicAdd(&S.ntouched, 1)] = slot;
+            },
+            [&](int, int) {}, S.lens, CW_LENS);
+        const int nt = S.ntouched;
         long long su = 0;
-        for (int i = lane; i <= (int)mask; i += 32) {
-            const int c = S.hc[i];
+        for (int i = lane; i < nt; i += 32) {
+            const int slot = S.touched[i];
+            const int c = S.hc[slot];
             if (c >= 2) {
                 su += c2(c);
-                add64(&vacc[S.hk[i]].C4, c2(c));
+                add64(&vacc[S.hk[slot]].C4, c2(c));
             }
         }
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
-        if (!su) continue;   // no 4-cycle rooted at u: middle vertices get nothing
-        S.pv[lane] = 0;
+        if (su) {   // middle vertices, only when some cycle is rooted at u
+            S.pv[lane] = 0;
+            __syncwarp();
+            walk_wedges(
+                g, u, b, din, 0, 1, S.sst, S.spre,
+                [&](int q, int pos) {
+                    const int c = hcount_get(S.hk, S.hc, mask, g.ncol[pos]);
+                    if (c > 1) atomicAdd((unsigned long long *)&S.pv[q], (unsigned long long)(c - 1));
+                },
+                [&](int v, int) {
+                    const long long x = S.pv[lane];
+                    if (x) add64(&vacc[v].C4, x);
+                    S.pv[lane] = 0;
+                },
+                S.lens, CW_LENS);
+        }
+        for (int i = lane; i < nt; i += 32) {
+            const int slot = S.touched[i];
+            S.hk[slot] = -1;
+            S.hc[slot] = 0;
+        }
         __syncwarp();
-        walk_wedges(g, u, b, din, 0, 1, S.sst, S.spre,
-                    [&](int q, int pos) {
-                        const int c = hcount_get(S.hk, S.hc, mask, g.ncol[pos]);
-                        if (c > 1) atomicAdd((unsigned long long *)&S.pv[q], (unsigned long long)(c - 1));
-                    },
-                    [&](int v, int) {
-                        const long long x = S.pv[lane];
-                        if (x) add64(&vacc[v].C4, x);
-                        S.pv[lane] = 0;
-                    });
+        if (lane == 0) S.ntouched = 0;
+        __syncwarp();
     }
 }
 

@@ -178,7 +178,13 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     const bool batch = vtx_offset != nullptr;
     const Layout L = plan(n, m, ds->num_sms, batch);
     void *base = nullptr;
-    if (cudaMallocFromPoolAsync(&base, L.total, ds->pool, st) != cudaSuccess) {
+    // Inside stream capture the work memory becomes a graph allocation node
+    // (plain stream-ordered allocation); otherwise it comes from the pool.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return NIORCA_ECUDA;
+    const cudaError_t ae = cap == cudaStreamCaptureStatusActive ? cudaMallocAsync(&base, L.total, st)
+                                                                 : cudaMallocFromPoolAsync(&base, L.total, ds->pool, st);
+    if (ae != cudaSuccess) {
         cudaGetLastError();
         return NIORCA_ENOMEM;
     }

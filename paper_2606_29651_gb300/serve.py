@@ -1,0 +1,208 @@
+"""Continuous-batching server for orbit-count requests.
+
+Requests (one graph each, CSR in host memory) arrive at any time. A
+scheduler thread admits them in arrival order while their device footprint
+fits a memory budget, packs every admitted group into one niorca_count_batch
+call on one of several CUDA streams, and keeps up to `streams` such batches
+in flight: graphs that arrive while others are on the GPU join the next batch
+as soon as a stream and enough memory are free, and its copies and kernels
+overlap with the batches already running. A request's latency runs from
+submit() to the moment its counts are in host memory.
+
+The counts of a graph do not depend on which other graphs share its batch
+(the batched call counts the disjoint union, and no graphlet spans two
+components), so every result is identical alone and in the mix.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+class Request:
+    __slots__ = ("rowptr", "colidx", "n", "m", "future", "t_submit", "t_done")
+
+    def __init__(self, rowptr: np.ndarray, colidx: np.ndarray):
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self.colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        self.n = len(self.rowptr) - 1
+        self.m = len(self.colidx)
+        self.future: Future = Future()
+        self.t_submit = time.perf_counter()
+        self.t_done = None
+
+
+def footprint(num_graphs: int, total_n: int, total_m: int) -> int:
+    """Device bytes one batch holds while in flight: CSR, offsets, output and
+    the library's work memory."""
+    io = 4 * (total_n + 1) + 4 * total_m + 16 * (num_graphs + 1) + 120 * total_n
+    return io + _lib.batch_workspace_bytes(num_graphs, total_n, total_m)
+
+
+class _Batch:
+    def __init__(self, reqs, stream, nbytes):
+        self.reqs = reqs
+        self.stream = stream
+        self.nbytes = nbytes
+        self.event = torch.cuda.Event()
+        self.host_out = None
+        self.keep = None
+
+
+class Server:
+    """Continuous batching over `streams` CUDA streams within `mem_budget` bytes."""
+
+    def __init__(self, device: int | torch.device = 0, mem_budget: int = 8 << 30, streams: int = 3,
+                 max_batch_graphs: int = 4096, max_batch_edges: int = 64 << 20):
+        self.device = torch.device("cuda", device) if isinstance(device, int) else device
+        self.mem_budget = int(mem_budget)
+        self.max_batch_graphs = int(max_batch_graphs)
+        self.max_batch_edges = int(max_batch_edges)
+        with torch.cuda.device(self.device):
+            self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
+        self._pending: collections.deque = collections.deque()
+        self._inflight: list[_Batch] = []
+        self._free_streams = list(self.streams)
+        self._in_use = 0
+        self._cv = threading.Condition()
+        self._stop = False
+        self.completed = 0
+        self.batches = 0
+        self._thread = threading.Thread(target=self._loop, name="niorca-server", daemon=True)
+        self._thread.start()
+
+    # -------------------------------------------------------------- client
+    def submit(self, rowptr: np.ndarray, colidx: np.ndarray) -> Future:
+        """Queue one graph; the future resolves to its int64 [n, 15] counts."""
+        r = Request(rowptr, colidx)
+        r.future.request = r   # submit / completion times for latency statistics
+        if footprint(1, max(r.n, 1), r.m) > self.mem_budget:
+            r.future.set_exception(_lib.NiorcaError(_lib.Status.ENOMEM, "request larger than the memory budget"))
+            return r.future
+        with self._cv:
+            if self._stop:
+                raise RuntimeError("server is shut down")
+            self._pending.append(r)
+            self._cv.notify()
+        return r.future
+
+    def shutdown(self, wait: bool = True) -> None:
+        with self._cv:
+            self._stop = True
+            self._cv.notify()
+        if wait:
+            self._thread.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.shutdown()
+
+    # ----------------------------------------------------------- scheduler
+    def _admit(self):
+        """Pop the longest prefix of the queue that fits the free memory."""
+        take, n, m = [], 0, 0
+        while self._pending and len(take) < self.max_batch_graphs:
+            r = self._pending[0]
+            need = footprint(len(take) + 1, n + r.n, m + r.m)
+            if take and (need > self.mem_budget - self._in_use or m + r.m > self.max_batch_edges):
+                break
+            if not take and need > self.mem_budget - self._in_use:
+                break            # wait for memory to free up
+            take.append(self._pending.popleft())
+            n += r.n
+            m += r.m
+        return take, footprint(len(take), n, m) if take else 0
+
+    def _launch(self, reqs, nbytes):
+        stream = self._free_streams.pop()
+        b = _Batch(reqs, stream, nbytes)
+        ns = np.array([r.n for r in reqs], dtype=np.int64)
+        ms = np.array([r.m for r in reqs], dtype=np.int64)
+        vo = np.zeros(len(reqs) + 1, dtype=np.int64)
+        eo = np.zeros(len(reqs) + 1, dtype=np.int64)
+        vo[1:] = np.cumsum(ns)
+        eo[1:] = np.cumsum(ms)
+        total_n, total_m = int(vo[-1]), int(eo[-1])
+        rowptr = torch.empty(total_n + 1, dtype=torch.int32).pin_memory()
+        colidx = torch.empty(max(total_m, 1), dtype=torch.int32).pin_memory()
+        rp, ci = rowptr.numpy(), colidx.numpy()
+        for g, r in enumerate(reqs):
+            rp[vo[g]:vo[g + 1]] = r.rowptr[:-1] + eo[g]
+            ci[eo[g]:eo[g + 1]] = r.colidx
+        rp[-1] = total_m
+        offs = torch.from_numpy(np.concatenate([vo, eo])).pin_memory()
+        host_out = torch.empty((total_n, 15), dtype=torch.int64).pin_memory()
+        with torch.cuda.stream(stream):
+            d_rp = rowptr.to(self.device, non_blocking=True)
+            d_ci = colidx[:total_m].to(self.device, non_blocking=True)
+            d_off = offs.to(self.device, non_blocking=True)
+            out = torch.empty((total_n, 15), dtype=torch.int64, device=self.device)
+            _lib.count_batch(d_rp, d_ci, d_off[:len(reqs) + 1], d_off[len(reqs) + 1:], out, stream=stream)
+            host_out.copy_(out, non_blocking=True)
+            b.event.record(stream)
+        b.host_out = host_out
+        b.keep = (rowptr, colidx, offs, d_rp, d_ci, d_off, out, vo)
+        self._in_use += nbytes
+        self._inflight.append(b)
+        self.batches += 1
+
+    def _retire(self, b: _Batch, now: float):
+        vo = b.keep[-1]
+        err = None
+        try:
+            _lib.check(b.stream)
+        except _lib.NiorcaError as e:
+            err = e
+        res = b.host_out.numpy()
+        for g, r in enumerate(b.reqs):
+            r.t_done = now
+            if err is not None:
+                r.future.set_exception(err)
+            else:
+                r.future.set_result(res[vo[g]:vo[g + 1]].copy())
+        self.completed += len(b.reqs)
+        self._in_use -= b.nbytes
+        self._free_streams.append(b.stream)
+        b.keep = None
+
+    def _loop(self):
+        torch.cuda.set_device(self.device)
+        while True:
+            with self._cv:
+                if self._stop and not self._pending and not self._inflight:
+                    return
+                if not self._pending and not self._inflight:
+                    self._cv.wait(timeout=0.05)
+                    continue
+            now = time.perf_counter()
+            for b in [b for b in self._inflight if b.event.query()]:
+                self._inflight.remove(b)
+                self._retire(b, now)
+            launched = False
+            with self._cv:
+                if self._pending and self._free_streams:
+                    reqs, nbytes = self._admit()
+                else:
+                    reqs, nbytes = [], 0
+            if reqs:
+                self._launch(reqs, nbytes)
+                launched = True
+            if not launched:
+                time.sleep(20e-6)
+
+
+def latency_stats(requests_latency_s) -> dict:
+    a = np.sort(np.asarray(requests_latency_s, dtype=np.float64))
+    if len(a) == 0:
+        return {"p50_ms": None, "p99_ms": None}
+    return {"p50_ms": float(np.percentile(a, 50) * 1e3), "p99_ms": float(np.percentile(a, 99) * 1e3),
+            "mean_ms": float(a.mean() * 1e3), "max_ms": float(a.max() * 1e3)}
