@@ -138,6 +138,23 @@ int32_t niorca_version(void);
  *   niorca_launch_count    kernels launched by the library since it was
  *                          loaded, timing on or off.
  */
+/*
+ * Tuning of the launch shape (no counterpart in the paper, whose knobs are
+ * OpenMP schedules and chunk sizes, Sec. 8). values[i] for i < count sets,
+ * for the current device and every later call on it:
+ *   0..4  CTAs per SM of the relabel, triangle, edge-aggregate, 4-cycle and
+ *         solve kernels (1..64; defaults 8, 8, 8, 16, 8)
+ *   5     degree class from which a row is relabelled by a whole CTA
+ *         (1..127; default 32, i.e. degree >= 512)
+ *   6     largest wedge count of a 4-cycle root handled by one warp (2..512)
+ *   7     largest out-degree of a triangle root handled by one warp (2..64)
+ * Any setting gives the same counts; only the speed changes. Returns
+ * NIORCA_EINVAL (and changes nothing) for a value out of range.
+ * niorca_get_tuning copies the current values and returns how many exist.
+ */
+niorca_status niorca_set_tuning(const int32_t *values, int32_t count);
+int32_t niorca_get_tuning(int32_t *values, int32_t count);
+
 void niorca_profile_enable(int32_t on);
 int32_t niorca_profile_read(double *ms, int64_t *launches, int32_t max_kernels);
 void niorca_profile_reset(void);

@@ -68,6 +68,10 @@ def _lib():
     h.niorca_kernel_name.argtypes = [i32]
     h.niorca_launch_count.restype = i64
     h.niorca_launch_count.argtypes = []
+    h.niorca_set_tuning.restype = ctypes.c_int
+    h.niorca_set_tuning.argtypes = [vp, i32]
+    h.niorca_get_tuning.restype = i32
+    h.niorca_get_tuning.argtypes = [vp, i32]
     _handle = h
     return h
 
@@ -191,3 +195,28 @@ def profile_read() -> dict:
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(_lib().niorca_launch_count())
+
+
+TUNING_KEYS = ("grid_relabel", "grid_tri", "grid_agg", "grid_c4", "grid_solve", "long_row_class", "c4_warp_maxw",
+               "warp_maxd")
+
+
+def get_tuning() -> dict:
+    import numpy as np
+    v = np.zeros(len(TUNING_KEYS), dtype=np.int32)
+    _lib().niorca_get_tuning(v.ctypes.data, len(v))
+    return dict(zip(TUNING_KEYS, (int(x) for x in v)))
+
+
+def set_tuning(**kw) -> None:
+    """Set launch-shape knobs by name (see niorca_set_tuning); others keep their value."""
+    import numpy as np
+    cur = get_tuning()
+    for k, val in kw.items():
+        if k not in cur:
+            raise KeyError(k)
+        cur[k] = int(val)
+    v = np.array([cur[k] for k in TUNING_KEYS], dtype=np.int32)
+    st = _lib().niorca_set_tuning(v.ctypes.data, len(v))
+    if st:
+        raise NiorcaError(st, "niorca_set_tuning")

@@ -108,7 +108,8 @@ __device__ __forceinline__ int hcount_add_new(int *keys, int *cnts, unsigned mas
 
 // One warp per root with at most CW_MAXW wedges. The table is cleared once
 // per warp; afterwards every root empties only the slots it filled.
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters) {
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters,
+                                                           int maxw) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
         }
         W = warp_sum(W);
         if (W < 2) continue;
-        if (W > CW_MAXW) {
+        if (W > maxw) {
             if (lane == 0) {
                 if (W > CC_MAXW) glob_list[atomicAdd(&counters[CNT_C4_GLOBAL], 1)] = u;
                 else cta_list[atomicAdd(&counters[CNT_C4_CTA], 1)] = u;
@@ -297,7 +298,8 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
 
 void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
-    k_c4_warp<<<w.num_sms * 16, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters);
+    const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
+    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw);
     after_launch(st, K_C4_WARP);
     k_c4_cta<<<w.num_sms * 2, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters);
     after_launch(st, K_C4_CTA);

@@ -26,6 +26,21 @@ struct Work {
     int c4slots = 0;         // rows in c4dense (each n ints)
     int *status = nullptr;   // device status word (not part of the carve)
     int num_sms = 0;
+    int tune[8] = {8, 8, 8, 16, 8, 32, 512, 64};  // see TuneIndex
+};
+
+// Runtime tuning knobs (niorca_set_tuning): CTAs per SM of the persistent
+// warp-tier kernels, and the thresholds that route vertices to a warp or a CTA.
+enum TuneIndex {
+    TUNE_GRID_RELABEL = 0,   // k_relabel_rows_warp CTAs per SM
+    TUNE_GRID_TRI = 1,       // k_tri_warp
+    TUNE_GRID_AGG = 2,       // k_agg_warp
+    TUNE_GRID_C4 = 3,        // k_c4_warp
+    TUNE_GRID_SOLVE = 4,     // k_solve
+    TUNE_LONG_ROW_CLASS = 5, // degree class from which a row is relabelled by a whole CTA
+    TUNE_C4_WARP_MAXW = 6,   // largest wedge count of a 4-cycle root kept in one warp (<= 512)
+    TUNE_WARP_MAXD = 7,      // largest out-degree of a triangle root kept in one warp (<= 64)
+    TUNE_COUNT = 8
 };
 
 // Indices into Work::counters.

@@ -96,6 +96,7 @@ struct DeviceState {
     cudaMemPool_t pool = nullptr;
     int *status = nullptr;
     int num_sms = 0;
+    int tune[TUNE_COUNT] = {8, 8, 8, 16, 8, 32, 512, 64};
 };
 
 constexpr int MAX_DEVICES = 64;
@@ -209,6 +210,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     w.c4slots = L.c4slots;
     w.status = ds->status;
     w.num_sms = ds->num_sms;
+    for (int i = 0; i < TUNE_COUNT; ++i) w.tune[i] = ds->tune[i];
     cudaMemsetAsync(w.counters, 0, 4 * 16, st);
     timeline_begin(st);
     if (batch) {
@@ -332,3 +334,34 @@ extern "C" void niorca_profile_reset(void) {
 extern "C" const char *niorca_kernel_name(int32_t id) { return kernel_name(id); }
 
 extern "C" int64_t niorca_launch_count(void) { return g_launches.load(); }
+
+namespace {
+bool tune_valid(int i, int v) {
+    switch (i) {
+    case TUNE_LONG_ROW_CLASS: return v >= 1 && v < NCLASS;
+    case TUNE_C4_WARP_MAXW: return v >= 2 && v <= 512;
+    case TUNE_WARP_MAXD: return v >= 2 && v <= 64;
+    default: return v >= 1 && v <= 64;   // CTAs per SM
+    }
+}
+}  // namespace
+
+extern "C" niorca_status niorca_set_tuning(const int32_t *values, int32_t count) {
+    if (!values || count < 0 || count > TUNE_COUNT) return NIORCA_EINVAL;
+    for (int i = 0; i < count; ++i)
+        if (!tune_valid(i, values[i])) return NIORCA_EINVAL;
+    DeviceState *ds = nullptr;
+    niorca_status s = device_state(&ds);
+    if (s != NIORCA_OK) return s;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int i = 0; i < count; ++i) ds->tune[i] = values[i];
+    return NIORCA_OK;
+}
+
+extern "C" int32_t niorca_get_tuning(int32_t *values, int32_t count) {
+    DeviceState *ds = nullptr;
+    if (device_state(&ds) != NIORCA_OK) return 0;
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int i = 0; i < count && i < TUNE_COUNT; ++i) values[i] = ds->tune[i];
+    return TUNE_COUNT;
+}

@@ -211,11 +211,12 @@ __device__ __forceinline__ long long c2m1(int d) {  // C(d - 1, 2)
 __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, const int *colidx, int n,
                                                            const int2 *vrange, const int2 *vinfo, const int *perm,
                                                            const int *nrow, const int *coff, int ntiles, int *ncol,
-                                                           int *split, VAcc *vacc, int *tcnt, int *status) {
+                                                           int *split, VAcc *vacc, int *tcnt, int *status,
+                                                           int long_class) {
     __shared__ int hist_all[8][NCLASS];
     const int lane = lane_id();
     int *H = hist_all[threadIdx.x >> 5];
-    const int bound = coff[LONG_ROW_CLASS * ntiles];
+    const int bound = coff[long_class * ntiles];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     int bad = 0;
@@ -298,14 +299,14 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
                                                                   const int *perm,
                                                                   const int *nrow, const int *coff, int ntiles,
                                                                   int *ncol, int *split, VAcc *vacc, int *tcnt,
-                                                                  int *status) {
+                                                                  int *status, int long_class) {
     constexpr int NW = RLC_THREADS / 32;
     __shared__ int H[NCLASS];
     __shared__ int tot[NCLASS];
     __shared__ int wc[NW][NCLASS];
     __shared__ long long red[3][NW];
     const int lane = lane_id(), w = threadIdx.x >> 5;
-    const int bound = coff[LONG_ROW_CLASS * ntiles];
+    const int bound = coff[long_class * ntiles];
     int bad = 0;
     for (int r = bound + blockIdx.x; r < n; r += gridDim.x) {
         const int x = perm[r];
@@ -396,12 +397,14 @@ static void relabel_common(const int *rowptr, const int *colidx, const int2 *vra
     k_class_scatter<<<nt, RL_THREADS, 0, st>>>(w.n, w.vinfo, w.coff, nt, w.perm, w.split);
     after_launch(st, K_CLASS_SCATTER);
     launch_exclusive_scan(w.split, w.nrow, w.n, true, w.scan_part, st);
-    k_relabel_rows_warp<<<w.num_sms * 8, 256, 0, st>>>(rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow, w.coff,
-                                                       nt, w.ncol, w.split, w.vacc, w.tcnt, w.status);
+    const int lrc = w.tune[TUNE_LONG_ROW_CLASS];
+    k_relabel_rows_warp<<<w.num_sms * w.tune[TUNE_GRID_RELABEL], 256, 0, st>>>(
+        rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow, w.coff, nt, w.ncol, w.split, w.vacc, w.tcnt, w.status,
+        lrc);
     after_launch(st, K_RELABEL_WARP);
     k_relabel_rows_cta<<<w.num_sms * 2, RLC_THREADS, 0, st>>>(rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow,
                                                               w.coff, nt, w.ncol, w.split, w.vacc, w.tcnt,
-                                                              w.status);
+                                                              w.status, lrc);
     after_launch(st, K_RELABEL_CTA);
 }
 

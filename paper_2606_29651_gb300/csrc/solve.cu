@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
-    k_solve<<<w.num_sms * 8, 256, 0, st>>>(g, w.vacc, w.perm, out);
+    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], 256, 0, st>>>(g, w.vacc, w.perm, out);
     after_launch(st, K_SOLVE);
 }
 

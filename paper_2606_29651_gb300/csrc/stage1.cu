@@ -45,7 +45,7 @@ struct TriWarpSmem {
 };
 
 __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, VAcc *vacc, int *heavy,
-                                                            int *counters) {
+                                                            int *counters, int maxd) {
     __shared__ TriWarpSmem sm_all[TW_WARPS];
     TriWarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
     for (int u = gw; u < g.n; u += nw) {
         const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
         if (dp < 2) continue;
-        if (dp > TW_MAXD) {
+        if (dp > maxd) {
             if (lane == 0) heavy[atomicAdd(&counters[CNT_TRI_HEAVY], 1)] = u;
             continue;
         }
@@ -280,7 +280,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
 
 void launch_stage1(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
-    k_tri_warp<<<w.num_sms * 8, TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    const int maxd = w.tune[TUNE_WARP_MAXD] < TW_MAXD ? w.tune[TUNE_WARP_MAXD] : TW_MAXD;
+    k_tri_warp<<<w.num_sms * w.tune[TUNE_GRID_TRI], TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
+                                                                          maxd);
     after_launch(st, K_TRI_WARP);
     k_tri_cta<<<w.num_sms * 1, TC_THREADS, TC_SMEM_MAX, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
     after_launch(st, K_TRI_CTA);

@@ -65,7 +65,7 @@ __device__ __forceinline__ bool edge_aggregates(const Graph &g, const int *tcnt,
 }
 
 __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *tcnt, VAcc *vacc, int *heavy,
-                                                            int *counters) {
+                                                            int *counters, int maxd) {
     __shared__ AggWarpSmem sm_all[AW_WARPS];
     AggWarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
     for (int u = gw; u < g.n; u += nw) {
         const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
         if (dp < 1) continue;
-        if (dp > AW_MAXD) {
+        if (dp > maxd) {
             if (lane == 0) heavy[atomicAdd(&counters[CNT_AGG_HEAVY], 1)] = u;
             continue;
         }
@@ -216,7 +216,9 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
 void launch_stage2(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
     int *heavy = w.lists + (size_t)w.n;
-    k_agg_warp<<<w.num_sms * 8, AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    const int maxd = w.tune[TUNE_WARP_MAXD] < AW_MAXD ? w.tune[TUNE_WARP_MAXD] : AW_MAXD;
+    k_agg_warp<<<w.num_sms * w.tune[TUNE_GRID_AGG], AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters,
+                                                                          maxd);
     after_launch(st, K_AGG_WARP);
     k_agg_cta<<<w.num_sms, AC_THREADS, AC_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
     after_launch(st, K_AGG_CTA);

@@ -97,3 +97,25 @@ def test_batch_in_captured_cuda_graph(ni):
         torch.cuda.synchronize()
         assert torch.equal(out.cpu(), ref)
     ni.check()
+
+
+def test_tuning_knobs_do_not_change_counts(ni, tmp_path, monkeypatch):
+    from paper_2606_29651_gb300 import autotune
+    monkeypatch.setenv("NIORCA_TUNING_CACHE", str(tmp_path / "tuning.json"))
+    rp, ci = gg.rmat(13, 16, seed=21)
+    exp = _alone(ni, rp, ci)
+    saved = ni.get_tuning()
+    try:
+        for knobs in ({"warp_maxd": 2, "c4_warp_maxw": 2, "long_row_class": 1},
+                      {"grid_tri": 1, "grid_c4": 1, "grid_relabel": 1, "grid_agg": 1, "grid_solve": 1},
+                      {"warp_maxd": 33, "c4_warp_maxw": 100, "long_row_class": 20}):
+            ni.set_tuning(**knobs)
+            assert np.array_equal(_alone(ni, rp, ci), exp), knobs
+        dev = torch.device("cuda:0")
+        res = autotune.tune_graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev), reps=1)
+        assert set(res["params"]) == set(saved) and not res["cached"]
+        assert np.array_equal(_alone(ni, rp, ci), exp)
+        again = autotune.tune_graph(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
+        assert again["cached"] and again["params"] == res["params"]
+    finally:
+        ni.set_tuning(**saved)
