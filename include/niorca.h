@@ -72,6 +72,16 @@ niorca_status niorca_count(const int32_t *rowptr, const int32_t *colidx, int32_t
                            int64_t *out, void *stream);
 
 /*
+ * INDUCED orbit counts psi'_k(v) of one graph: the graphlet must be the
+ * subgraph induced by its vertices (Def. 2), the variant ORCA counts and
+ * that Sec. 5 contrasts with NI-ORCA (psi'13, psi'11, psi'10 are printed
+ * there). Computed from the non-induced counts of the same three stages;
+ * arguments and errors as niorca_count.
+ */
+niorca_status niorca_count_induced(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                                   int64_t *out, void *stream);
+
+/*
  * Orbit counts of many independent graphs in one call (the same stages for
  * each graph; graphs are packed back to back).
  *   rowptr      device int32[total_n + 1]: the concatenation of every

@@ -13,6 +13,8 @@ counts of the 15 non-induced graphlet orbits on up to four vertices
     every connected spanning edge subset, classified.
   * ``brute_count`` (``brute.py``): the definition over all vertex subsets in
     pure Python, for graphs of about a dozen vertices.
+  * ``induced_count``: induced orbit counts (Def. 2: E' = every edge inside
+    V'), by the same enumeration.
 
 Every function here is pinned by the tests (closed forms, invariants, brute
 force). Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
@@ -77,6 +79,8 @@ def _load():
     lib.orc_max_threads.argtypes = []
     lib.def_count.restype = None
     lib.def_count.argtypes = [i32, vp, vp, vp]
+    lib.def_count_induced.restype = None
+    lib.def_count_induced.argtypes = [i32, vp, vp, vp]
     lib.def_count_vertices.restype = None
     lib.def_count_vertices.argtypes = [i32, vp, vp, i32, vp, vp]
     _lib = lib
@@ -154,3 +158,11 @@ def definition_count_vertices(rowptr, colidx, verts) -> np.ndarray:
     out = np.zeros((max(len(v), 1), 15), dtype=np.int64)
     _load().def_count_vertices(n, rp.ctypes.data, ci.ctypes.data, len(v), v.ctypes.data, out.ctypes.data)
     return out[:len(v)]
+
+
+def induced_count(rowptr, colidx) -> np.ndarray:
+    """Induced orbit counts of every vertex by enumeration (Def. 2); int64[n, 15]."""
+    n, rp, ci = _csr(rowptr, colidx)
+    out = np.zeros((max(n, 1), 15), dtype=np.int64)
+    _load().def_count_induced(n, rp.ctypes.data, ci.ctypes.data, out.ctypes.data)
+    return out[:n]

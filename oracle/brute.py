@@ -53,8 +53,10 @@ def _orbit(k: int, nedges: int, degs: dict, v) -> int:
     return 14                            # K4
 
 
-def brute_count(n: int, edges) -> list:
-    """psi[x][k] for every vertex x of the simple graph (range(n), edges)."""
+def brute_count(n: int, edges, induced: bool = False) -> list:
+    """psi[x][k] for every vertex x of the simple graph (range(n), edges).
+
+    With induced=True only E' = all edges inside V' is counted (Def. 2)."""
     adj = [set() for _ in range(n)]
     for a, b in edges:
         if a != b:
@@ -63,9 +65,10 @@ def brute_count(n: int, edges) -> list:
     psi = [[0] * 15 for _ in range(n)]
     for k in (2, 3, 4):
         for vs in itertools.combinations(range(n), k):
-            induced = [(a, b) for a, b in itertools.combinations(vs, 2) if b in adj[a]]
-            for r in range(k - 1, len(induced) + 1):
-                for sub in itertools.combinations(induced, r):
+            inside = [(a, b) for a, b in itertools.combinations(vs, 2) if b in adj[a]]
+            sizes = [len(inside)] if induced else range(k - 1, len(inside) + 1)
+            for r in sizes:
+                for sub in itertools.combinations(inside, r):
                     if not _connected(list(vs), sub):
                         continue
                     degs = {v: 0 for v in vs}

@@ -65,12 +65,14 @@ static int uf_find(int *p, int a) {
  * If `only` >= 0, only that vertex is credited and `out` is its 15-entry row;
  * otherwise `out` is the n x 15 table.
  */
+static int g_induced = 0;  /* 1: only E' = every edge inside V' (Def. 2) */
+
 static void credit_set(const dgraph *g, const int32_t *s, int k, int64_t *out, int32_t only) {
     int ea[6], eb[6], ne = 0;
     for (int i = 0; i < k; ++i)
         for (int j = i + 1; j < k; ++j)
             if (adjacent(g, s[i], s[j])) { ea[ne] = i; eb[ne] = j; ++ne; }
-    for (int mask = 1; mask < (1 << ne); ++mask) {
+    for (int mask = g_induced ? (1 << ne) - 1 : 1; mask < (1 << ne); ++mask) {
         int dv[4] = {0, 0, 0, 0}, par[4] = {0, 1, 2, 3}, cnt = 0, comps = k;
         for (int e = 0; e < ne; ++e) {
             if (!((mask >> e) & 1)) continue;
@@ -145,6 +147,7 @@ static void esu_root(const dgraph *g, int32_t v, int whole, int64_t *out, int32_
 /* All vertices: out is n x 15 int64, zeroed here. */
 void def_count(int32_t n, const int32_t *rowptr, const int32_t *colidx, int64_t *out) {
     dgraph g = {n, rowptr, colidx};
+    g_induced = 0;
     memset(out, 0, sizeof(int64_t) * 15 * (size_t)n);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t v = 0; v < n; ++v) esu_root(&g, v, 1, out, -1);
@@ -158,6 +161,7 @@ void def_count(int32_t n, const int32_t *rowptr, const int32_t *colidx, int64_t 
 void def_count_vertices(int32_t n, const int32_t *rowptr, const int32_t *colidx, int32_t nq, const int32_t *verts,
                         int64_t *out) {
     dgraph g = {n, rowptr, colidx};
+    g_induced = 0;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t i = 0; i < nq; ++i) {
         int64_t *row = out + (size_t)i * 15;
@@ -166,4 +170,17 @@ void def_count_vertices(int32_t n, const int32_t *rowptr, const int32_t *colidx,
         if (x < 0 || x >= n) continue;
         esu_root(&g, x, 0, row, x);
     }
+}
+
+/*
+ * Induced orbit counts by definition (Def. 2: E' is every edge of G inside
+ * V'): the same enumeration with only the full induced edge set kept.
+ */
+void def_count_induced(int32_t n, const int32_t *rowptr, const int32_t *colidx, int64_t *out) {
+    dgraph g = {n, rowptr, colidx};
+    memset(out, 0, sizeof(int64_t) * 15 * (size_t)n);
+    g_induced = 1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t v = 0; v < n; ++v) esu_root(&g, v, 1, out, -1);
+    g_induced = 0;
 }

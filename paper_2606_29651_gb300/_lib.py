@@ -44,6 +44,8 @@ def _lib():
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     h.niorca_count.restype = ctypes.c_int
     h.niorca_count.argtypes = [vp, vp, i32, i64, vp, vp]
+    h.niorca_count_induced.restype = ctypes.c_int
+    h.niorca_count_induced.argtypes = [vp, vp, i32, i64, vp, vp]
     h.niorca_count_batch.restype = ctypes.c_int
     h.niorca_count_batch.argtypes = [vp, vp, vp, vp, i32, i64, i64, vp, vp]
     h.niorca_validate.restype = ctypes.c_int
@@ -118,6 +120,24 @@ def count(rowptr: torch.Tensor, colidx: torch.Tensor, out: torch.Tensor | None =
     st = _lib().niorca_count(_ptr(rowptr), _ptr(colidx), n, colidx.numel(), _ptr(out), _stream_ptr(stream))
     if st:
         raise NiorcaError(st, "niorca_count")
+    return out
+
+
+def count_induced(rowptr: torch.Tensor, colidx: torch.Tensor, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Induced orbit counts psi'[v, k] (Def. 2), same conventions as count()."""
+    _dev(rowptr, torch.int32, "rowptr")
+    _dev(colidx, torch.int32, "colidx")
+    n = rowptr.numel() - 1
+    if out is None:
+        out = torch.empty((max(n, 0), 15), dtype=torch.int64, device=rowptr.device)
+    _dev(out, torch.int64, "out")
+    if out.numel() != 15 * max(n, 0):
+        raise ValueError("out must hold n * 15 int64")
+    st = _lib().niorca_count_induced(_ptr(rowptr), _ptr(colidx), n, colidx.numel(), _ptr(out),
+                                     _stream_ptr(stream))
+    if st:
+        raise NiorcaError(st, "niorca_count_induced")
     return out
 
 

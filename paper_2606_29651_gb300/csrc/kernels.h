@@ -27,6 +27,7 @@ struct Work {
     int *status = nullptr;   // device status word (not part of the carve)
     int num_sms = 0;
     int tune[8] = {8, 8, 8, 16, 8, 32, 512, 64};  // see TuneIndex
+    int induced = 0;         // write induced instead of non-induced counts
 };
 
 // Runtime tuning knobs (niorca_set_tuning): CTAs per SM of the persistent

@@ -172,7 +172,7 @@ niorca_status check_launch() {
 
 // Runs the whole pipeline on one (possibly union) graph.
 niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long *out, cudaStream_t st,
-                  const long long *vtx_offset, const long long *edge_offset, int num_graphs) {
+                  const long long *vtx_offset, const long long *edge_offset, int num_graphs, int induced = 0) {
     DeviceState *ds = nullptr;
     niorca_status s = device_state(&ds);
     if (s != NIORCA_OK) return s;
@@ -211,6 +211,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     w.status = ds->status;
     w.num_sms = ds->num_sms;
     for (int i = 0; i < TUNE_COUNT; ++i) w.tune[i] = ds->tune[i];
+    w.induced = induced;
     cudaMemsetAsync(w.counters, 0, 4 * 16, st);
     timeline_begin(st);
     if (batch) {
@@ -242,6 +243,15 @@ extern "C" niorca_status niorca_count(const int32_t *rowptr, const int32_t *coli
     if (!rowptr || !out || (m > 0 && !colidx)) return NIORCA_EINVAL;
     return run(rowptr, colidx, n, (int)m, reinterpret_cast<long long *>(out), static_cast<cudaStream_t>(stream),
                nullptr, nullptr, 0);
+}
+
+extern "C" niorca_status niorca_count_induced(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                                              int64_t *out, void *stream) {
+    if (n < 0 || m < 0 || m > INT32_MAX) return NIORCA_EINVAL;
+    if (n == 0) return m == 0 ? NIORCA_OK : NIORCA_EINVAL;
+    if (!rowptr || !out || (m > 0 && !colidx)) return NIORCA_EINVAL;
+    return run(rowptr, colidx, n, (int)m, reinterpret_cast<long long *>(out), static_cast<cudaStream_t>(stream),
+               nullptr, nullptr, 0, 1);
 }
 
 extern "C" niorca_status niorca_count_batch(const int32_t *rowptr, const int32_t *colidx, const int64_t *vtx_offset,

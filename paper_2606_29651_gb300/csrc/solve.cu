@@ -50,7 +50,34 @@ __device__ __forceinline__ void orbit_equations(long long d, const VAcc &a, long
     psi[14] = a.K4;                            // K4[x] (Stage II)
 }
 
-__global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const int *perm, long long *out) {
+// Induced counts from non-induced ones. An induced graphlet with x in
+// orbit j contains a fixed number of spanning non-induced graphlets with x
+// in orbit k (psi = O psi', O unitriangular; e.g. a K4 holds six paths with
+// x at an end, three diamonds with x of degree 3). Back-substitution from
+// the densest graphlet down; the rows for o13, o11 and o10 are the induced
+// equations printed in Sec. 5 (psi'13 = f13/2 - 3 f14, psi'11 =
+// (f11 - f13)/2 + 3 f14, psi'10 = f10 - f13 + 6 f14).
+__device__ __forceinline__ void to_induced(long long *p) {
+    const long long i14 = p[14];
+    const long long i13 = p[13] - 3 * i14;
+    const long long i12 = p[12] - 3 * i14;
+    const long long i11 = p[11] - 2 * i13 - 3 * i14;
+    const long long i10 = p[10] - 2 * i12 - 2 * i13 - 6 * i14;
+    const long long i9 = p[9] - 2 * i12 - 3 * i14;
+    const long long i8 = p[8] - i12 - i13 - 3 * i14;
+    const long long i7 = p[7] - i11 - i13 - i14;
+    const long long i6 = p[6] - i9 - i10 - 2 * i12 - i13 - 3 * i14;
+    const long long i5 = p[5] - 2 * i8 - i10 - 2 * i11 - 2 * i12 - 4 * i13 - 6 * i14;
+    const long long i4 = p[4] - 2 * i8 - 2 * i9 - i10 - 4 * i12 - 2 * i13 - 6 * i14;
+    const long long i3 = p[3];
+    p[1] -= 2 * i3;
+    p[2] -= i3;
+    p[4] = i4; p[5] = i5; p[6] = i6; p[7] = i7; p[8] = i8; p[9] = i9;
+    p[10] = i10; p[11] = i11; p[12] = i12; p[13] = i13; p[14] = i14;
+}
+
+__global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const int *perm, long long *out,
+                                               int induced) {
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -68,6 +95,7 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
             const VAcc a = vacc[x];
             long long psi[15];
             orbit_equations(e - b, a, sS1, sA1 / 2, psi);
+            if (induced) to_induced(psi);
             long long v = psi[0];
 #pragma unroll
             for (int k = 1; k < 15; ++k)
@@ -79,7 +107,7 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
     Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
-    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], 256, 0, st>>>(g, w.vacc, w.perm, out);
+    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], 256, 0, st>>>(g, w.vacc, w.perm, out, w.induced);
     after_launch(st, K_SOLVE);
 }
 

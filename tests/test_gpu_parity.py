@@ -175,3 +175,17 @@ def test_validate_detects_asymmetry(ni):
     rp2, ci2 = gg.rmat(10, 8, seed=1)
     ni.validate(torch.from_numpy(rp2).to(dev), torch.from_numpy(ci2).to(dev))
     assert ni.last_status() == Status.OK
+
+
+@pytest.mark.parametrize("name,make", [
+    ("er400", lambda: gg.er(400, 0.06, 41)),
+    ("rmat10", lambda: gg.rmat(10, 16, seed=42)),
+    ("dense80", lambda: gg.er(80, 0.6, 43)),
+    ("k30", lambda: gg.complete(30)),
+])
+def test_induced_counts_vs_definition(ni, name, make):
+    rp, ci = make()
+    dev = torch.device("cuda:0")
+    out = ni.count_induced(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
+    ni.check()
+    assert_same(out.cpu().numpy(), oracle.induced_count(rp, ci), name)
