@@ -198,7 +198,7 @@ static inline int64_t tri_ab(const graph_t *g, const int32_t *tri, int32_t a, in
  * on entry and zero again on return (ARR (T) of Table 3).
  */
 static void count_f_vars(const graph_t *g, const int32_t *tri, int32_t x, int32_t *mark, int32_t *common,
-                         int64_t *tx, fvars *f, int flags) {
+                         int32_t *ymark, int64_t *tx, fvars *f, int flags) {
     memset(f, 0, sizeof(*f));
     const int64_t dx = deg(g, x);
     const int64_t b = g->rp[x], e = g->rp[x + 1];
@@ -243,18 +243,32 @@ static void count_f_vars(const graph_t *g, const int32_t *tri, int32_t x, int32_
     for (int64_t i = b; i < e; ++i) {
         const int32_t y = g->ci[i];
         const int64_t dy = deg(g, y), txy = tx[i - b];
+        /* without a Stage I table, |N(y) ∩ N(z)| is counted against a marker
+           array of N(y) when N(z) is the shorter row */
+        const int use_ymark = (tri == NULL) && dy >= 64;
+        if (use_ymark)
+            for (int64_t q = g->rp[y]; q < g->rp[y + 1]; ++q) ymark[g->ci[q]] = 1;
         for (int64_t q = g->rp[y]; q < g->rp[y + 1]; ++q) {
             const int32_t z = g->ci[q];
             if (z == x) continue;
             f->p1 += 1;
             if (mark[z]) continue;
-            const int64_t tyz = tri_ab(g, tri, y, q, z), dz = deg(g, z);
+            const int64_t dz = deg(g, z);
+            int64_t tyz;
+            if (use_ymark && dz < dy) {
+                tyz = 0;
+                for (int64_t r = g->rp[z]; r < g->rp[z + 1]; ++r) tyz += ymark[g->ci[r]];
+            } else {
+                tyz = tri_ab(g, tri, y, q, z);
+            }
             if (flags & ORC_READ_F69_EYZ) f->f6_9 += dy - 2 - tyz;
             else f->f6_9 += dy - 2 - txy;
             f->f9_12 += tyz;
             f->f4_8 += dz - 1 - tyz;
             f->f8_12 += common[z] - 1;
         }
+        if (use_ymark)
+            for (int64_t q = g->rp[y]; q < g->rp[y + 1]; ++q) ymark[g->ci[q]] = 0;
     }
     for (int64_t i = b; i < e; ++i) {
         const int32_t y = g->ci[i];
@@ -318,18 +332,20 @@ int orc_stage3(int32_t n, const int32_t *rowptr, const int32_t *colidx, const in
     {
         int32_t *mark = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
         int32_t *common = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+        int32_t *ymark = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
         int64_t *tx = (int64_t *)malloc(((size_t)max_degree(&g) + 1) * sizeof(int64_t));
-        if (!mark || !common || !tx) err |= ORC_ENOMEM;
+        if (!mark || !common || !ymark || !tx) err |= ORC_ENOMEM;
         else {
 #pragma omp for schedule(dynamic, 1)
             for (int32_t x = 0; x < n; ++x) {
                 fvars f;
-                count_f_vars(&g, tri, x, mark, common, tx, &f, flags);
+                count_f_vars(&g, tri, x, mark, common, ymark, tx, &f, flags);
                 err |= solve_equations(&f, deg(&g, x), K4[x], out + (size_t)x * 15, mutation);
             }
         }
         free(mark);
         free(common);
+        free(ymark);
         free(tx);
     }
     return err;
@@ -400,20 +416,22 @@ int orc_count_vertices(int32_t n, const int32_t *rowptr, const int32_t *colidx, 
     {
         int32_t *mark = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
         int32_t *common = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+        int32_t *ymark = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
         int64_t *tx = (int64_t *)malloc(((size_t)max_degree(&g) + 1) * sizeof(int64_t));
-        if (!mark || !common || !tx) err |= ORC_ENOMEM;
+        if (!mark || !common || !ymark || !tx) err |= ORC_ENOMEM;
         else {
 #pragma omp for schedule(dynamic, 1)
             for (int32_t i = 0; i < nq; ++i) {
                 const int32_t x = verts[i];
                 if (x < 0 || x >= n) { err |= ORC_EINVAL; continue; }
                 fvars f;
-                count_f_vars(&g, NULL, x, mark, common, tx, &f, flags);
+                count_f_vars(&g, NULL, x, mark, common, ymark, tx, &f, flags);
                 err |= solve_equations(&f, deg(&g, x), k4_of_vertex(&g, x), out + (size_t)i * 15, mutation);
             }
         }
         free(mark);
         free(common);
+        free(ymark);
         free(tx);
     }
     return err;

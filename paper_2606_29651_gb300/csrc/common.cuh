@@ -167,12 +167,13 @@ __host__ __device__ __forceinline__ unsigned next_pow2(unsigned v) {
 }
 
 // Work-memory views of one counting call (all device pointers).
+// rinfo[u] = {row start, split, row end, 0} of the relabelled row of u:
+// N-(u) = ncol[x, y), N+(u) = ncol[y, z), one 16-byte load per row.
 struct Graph {
     int n;              // vertices
     int m;              // CSR entries (2|E|)
-    const int *nrow;    // relabelled offsets, n + 1
+    const int4 *rinfo;  // row bounds of every relabelled vertex
     const int *ncol;    // relabelled neighbours, rows ascending
-    const int *split;   // split[u]: first position of row u holding an id > u
 };
 
 }  // namespace niorca

@@ -38,9 +38,11 @@ __device__ __forceinline__ int seg_owner3(const int *pre, int k) {
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
-// Wedge segment of in-neighbour position p of root u: [nrow[v], cut).
-__device__ __forceinline__ int wedge_cut(const Graph &g, int v, int u) {
-    return lower_bound(g.ncol, g.split[v], g.nrow[v + 1], u);
+// Wedges through in-neighbour v of root u: row v from its start up to the
+// position of u, which lies in v's out-part [rv.y, rv.z).
+__device__ __forceinline__ int wedge_len(const Graph &g, int v, int u) {
+    const int4 rv = g.rinfo[v];
+    return lower_bound(g.ncol, rv.y, rv.z, u) - rv.x;
 }
 
 // Walks the wedges of root u: for every chunk of 32 in-neighbours (starting
@@ -57,8 +59,9 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
         int v = -1, st = 0, len = 0;
         if (p < din) {
             v = g.ncol[b + p];
-            st = g.nrow[v];
-            len = p < nlens ? lens[p] : wedge_cut(g, v, u) - st;
+            const int4 rv = g.rinfo[v];
+            st = rv.x;
+            len = p < nlens ? lens[p] : lower_bound(g.ncol, rv.y, rv.z, u) - rv.x;
         }
         const int incl = warp_inclusive_scan(len);
         sst[lane] = st;
@@ -122,12 +125,12 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
     if (lane == 0) S.ntouched = 0;
     __syncwarp();
     for (int u = gw; u < g.n; u += nw) {
-        const int b = g.nrow[u], din = g.split[u] - b;
+        const int4 ru = g.rinfo[u];
+        const int b = ru.x, din = ru.y - ru.x;
         if (din < 2) continue;
         long long W = 0;
         for (int p = lane; p < din; p += 32) {
-            const int v = g.ncol[b + p];
-            const int len = wedge_cut(g, v, u) - g.nrow[v];
+            const int len = wedge_len(g, g.ncol[b + p], u);
             if (p < CW_LENS) S.lens[p] = len;
             W += len;
         }
@@ -201,7 +204,8 @@ __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, cons
     const int nh = counters[CNT_C4_CTA];
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
         const int u = cta_list[h];
-        const int b = g.nrow[u], din = g.split[u] - b;
+        const int4 ru = g.rinfo[u];
+        const int b = ru.x, din = ru.y - ru.x;
         for (int i = threadIdx.x; i < CC_SLOTS; i += CC_THREADS) { hk[i] = -1; hc[i] = 0; }
         pv[lane] = 0;
         __syncthreads();
@@ -263,7 +267,8 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
     const int nh = counters[CNT_C4_GLOBAL];
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
         const int u = glob_list[h];
-        const int b = g.nrow[u], din = g.split[u] - b;
+        const int4 ru = g.rinfo[u];
+        const int b = ru.x, din = ru.y - ru.x;
         pv[lane] = 0;
         walk_wedges(g, u, b, din, wid, NW, sst, spre, [&](int, int pos) { atomicAdd(&row[g.ncol[pos]], 1); },
                     [&](int, int) {});
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
 }
 
 void launch_cycle4(Work &w, cudaStream_t st) {
-    Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
+    Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
     k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw);
     after_launch(st, K_C4_WARP);

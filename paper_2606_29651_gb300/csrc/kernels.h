@@ -15,7 +15,8 @@ struct Work {
     int *chist = nullptr;    // class histogram, NCLASS x ntiles (class-major)
     int *coff = nullptr;     // exclusive scan of chist
     int *nrow = nullptr;     // relabelled offsets, n + 1
-    int *split = nullptr;    // first out-neighbour position of each row (also scan input)
+    int *split = nullptr;    // scan input: degree of each new id
+    int4 *rinfo = nullptr;   // {row start, split, row end, 0} per new id
     int *ncol = nullptr;     // relabelled neighbours, m
     int *tcnt = nullptr;     // triangle count of each out-entry (u, v), u < v; m
     VAcc *vacc = nullptr;    // per-vertex accumulators, n

@@ -133,7 +133,7 @@ niorca_status device_state(DeviceState **out) {
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t vinfo, perm, chist, coff, nrow, split, ncol, tcnt, vacc, scan_part, lists, counters, c4dense, vrange;
+    size_t vinfo, perm, chist, coff, nrow, split, rinfo, ncol, tcnt, vacc, scan_part, lists, counters, c4dense, vrange;
     size_t total;
     int ntiles, c4slots;
 };
@@ -153,6 +153,7 @@ Layout plan(long long n, long long m, int num_sms, bool batch) {
     L.coff = take(4 * NCLASS * nt);
     L.nrow = take(4 * (n + 1));
     L.split = take(4 * n);
+    L.rinfo = take(16 * n);
     L.ncol = take(4 * m);
     L.tcnt = take(4 * m);
     L.vacc = take(sizeof(VAcc) * n);
@@ -200,6 +201,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     w.coff = reinterpret_cast<int *>(b + L.coff);
     w.nrow = reinterpret_cast<int *>(b + L.nrow);
     w.split = reinterpret_cast<int *>(b + L.split);
+    w.rinfo = reinterpret_cast<int4 *>(b + L.rinfo);
     w.ncol = reinterpret_cast<int *>(b + L.ncol);
     w.tcnt = reinterpret_cast<int *>(b + L.tcnt);
     w.vacc = reinterpret_cast<VAcc *>(b + L.vacc);

@@ -211,7 +211,7 @@ __device__ __forceinline__ long long c2m1(int d) {  // C(d - 1, 2)
 __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, const int *colidx, int n,
                                                            const int2 *vrange, const int2 *vinfo, const int *perm,
                                                            const int *nrow, const int *coff, int ntiles, int *ncol,
-                                                           int *split, VAcc *vacc, int *tcnt, int *status,
+                                                           int4 *rinfo, VAcc *vacc, int *tcnt, int *status,
                                                            int long_class) {
     __shared__ int hist_all[8][NCLASS];
     const int lane = lane_id();
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
         below = warp_sum(below);
         const int sp = nb + below;
         if (lane == 0) {
-            split[r] = sp;
+            rinfo[r] = make_int4(nb, sp, nb + d, 0);
             VAcc a;
             a.S1 = s1; a.A1 = 0; a.P6 = p6; a.A2 = 0; a.A3 = 0; a.D12 = 0; a.K4 = 0; a.C4 = 0;
             vacc[r] = a;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
                                                                   const int2 *vrange, const int2 *vinfo,
                                                                   const int *perm,
                                                                   const int *nrow, const int *coff, int ntiles,
-                                                                  int *ncol, int *split, VAcc *vacc, int *tcnt,
+                                                                  int *ncol, int4 *rinfo, VAcc *vacc, int *tcnt,
                                                                   int *status, int long_class) {
     constexpr int NW = RLC_THREADS / 32;
     __shared__ int H[NCLASS];
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
             long long a = 0, b = 0, c = 0;
             for (int ww = 0; ww < NW; ++ww) { a += red[0][ww]; b += red[1][ww]; c += red[2][ww]; }
             const int sp = nb + (int)c;
-            split[r] = sp;
+            rinfo[r] = make_int4(nb, sp, nb + d, 0);
             VAcc v;
             v.S1 = a; v.A1 = 0; v.P6 = b; v.A2 = 0; v.A3 = 0; v.D12 = 0; v.K4 = 0; v.C4 = 0;
             vacc[r] = v;
@@ -399,11 +399,11 @@ static void relabel_common(const int *rowptr, const int *colidx, const int2 *vra
     launch_exclusive_scan(w.split, w.nrow, w.n, true, w.scan_part, st);
     const int lrc = w.tune[TUNE_LONG_ROW_CLASS];
     k_relabel_rows_warp<<<w.num_sms * w.tune[TUNE_GRID_RELABEL], 256, 0, st>>>(
-        rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow, w.coff, nt, w.ncol, w.split, w.vacc, w.tcnt, w.status,
+        rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow, w.coff, nt, w.ncol, w.rinfo, w.vacc, w.tcnt, w.status,
         lrc);
     after_launch(st, K_RELABEL_WARP);
     k_relabel_rows_cta<<<w.num_sms * 2, RLC_THREADS, 0, st>>>(rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow,
-                                                              w.coff, nt, w.ncol, w.split, w.vacc, w.tcnt,
+                                                              w.coff, nt, w.ncol, w.rinfo, w.vacc, w.tcnt,
                                                               w.status, lrc);
     after_launch(st, K_RELABEL_CTA);
 }

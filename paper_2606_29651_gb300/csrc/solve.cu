@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int x = gw; x < g.n; x += nw) {
-        const int b = g.nrow[x], e = g.nrow[x + 1];
+        const int4 rx = g.rinfo[x];
+        const int b = rx.x, e = rx.z;
         long long sS1 = 0, sA1 = 0;
         for (int p = b + lane; p < e; p += 32) {
             const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[p]]);
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
 }
 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
-    Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
+    Graph g{w.n, w.m, w.rinfo, w.ncol};
     k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], 256, 0, st>>>(g, w.vacc, w.perm, out, w.induced);
     after_launch(st, K_SOLVE);
 }

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int u = gw; u < g.n; u += nw) {
-        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        const int4 ru = g.rinfo[u];
+        const int s = ru.y, e = ru.z, dp = e - s;
         if (dp < 2) continue;
         if (dp > maxd) {
             if (lane == 0) heavy[atomicAdd(&counters[CNT_TRI_HEAVY], 1)] = u;
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
             const int j = jb + lane;
             int len = 0, vs = 0;
             if (j < dp - 1) {
-                const int v = g.ncol[s + j];
-                vs = g.split[v];
-                len = g.nrow[v + 1] - vs;
+                const int4 rv = g.rinfo[g.ncol[s + j]];
+                vs = rv.y;
+                len = rv.z - rv.y;
             }
             const int incl = warp_inclusive_scan(len);
             S.sst[lane] = vs;
@@ -163,7 +164,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
     const int nh = counters[CNT_TRI_HEAVY];
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
         const int u = heavy[h];
-        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        const int4 ru = g.rinfo[u];
+        const int s = ru.y, e = ru.z, dp = e - s;
         const bool use_bits = dp <= TC_BITMAT_MAXD;
         const bool use_hash = dp <= TC_HASH_MAXD;
         const unsigned H = use_hash ? next_pow2(2 * dp) : 0;
@@ -194,9 +196,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
             const int j = jb + lane;
             int len = 0, vs = 0;
             if (j < dp - 1) {
-                const int v = g.ncol[s + j];
-                vs = g.split[v];
-                len = g.nrow[v + 1] - vs;
+                const int4 rv = g.rinfo[g.ncol[s + j]];
+                vs = rv.y;
+                len = rv.z - rv.y;
             }
             const int incl = warp_inclusive_scan(len);
             sst[lane] = vs;
@@ -221,8 +223,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
                 } else {
                     // K4 with this triangle (u, v, w): x in N+(w) ∩ N+(u) ∩ N+(v)
                     const int v = g.ncol[s + jj];
-                    const int vs0 = g.split[v], ve0 = g.nrow[v + 1];
-                    const int ws0 = g.split[w], we0 = g.nrow[w + 1];
+                    const int4 rv = g.rinfo[v], rw = g.rinfo[w];
+                    const int vs0 = rv.y, ve0 = rv.z;
+                    const int ws0 = rw.y, we0 = rw.z;
                     for (int p = ws0; p < we0; ++p) {
                         const int x = g.ncol[p];
                         if (x > umax) break;
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
 }
 
 void launch_stage1(Work &w, cudaStream_t st) {
-    Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
+    Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxd = w.tune[TUNE_WARP_MAXD] < TW_MAXD ? w.tune[TUNE_WARP_MAXD] : TW_MAXD;
     k_tri_warp<<<w.num_sms * w.tune[TUNE_GRID_TRI], TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
                                                                           maxd);

@@ -39,13 +39,15 @@ struct AggWarpSmem {
 // Edge aggregates of u's out-edges; returns whether any has a triangle.
 __device__ __forceinline__ bool edge_aggregates(const Graph &g, const int *tcnt, VAcc *vacc, int u, int s, int dp,
                                                 int first, int stride) {
-    const int du = g.nrow[u + 1] - g.nrow[u];
+    const int4 ru = g.rinfo[u];
+    const int du = ru.z - ru.x;
     long long a1 = 0, a2 = 0, a3 = 0;
     for (int j = first; j < dp; j += stride) {
         const long long t = tcnt[s + j];
         if (!t) continue;
         const int v = g.ncol[s + j];
-        const long long dv = g.nrow[v + 1] - g.nrow[v];
+        const int4 rv = g.rinfo[v];
+        const long long dv = rv.z - rv.x;
         a1 += t;
         a2 += t * t;
         a3 += t * dv;
@@ -72,7 +74,8 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int u = gw; u < g.n; u += nw) {
-        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        const int4 ru = g.rinfo[u];
+        const int s = ru.y, e = ru.z, dp = e - s;
         if (dp < 1) continue;
         if (dp > maxd) {
             if (lane == 0) heavy[atomicAdd(&counters[CNT_AGG_HEAVY], 1)] = u;
@@ -91,9 +94,9 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
             const int j = jb + lane;
             int len = 0, vs = 0;
             if (j < dp - 1 && tcnt[s + j] > 0) {
-                const int v = g.ncol[s + j];
-                vs = g.split[v];
-                len = g.nrow[v + 1] - vs;
+                const int4 rv = g.rinfo[g.ncol[s + j]];
+                vs = rv.y;
+                len = rv.z - rv.y;
             }
             const int incl = warp_inclusive_scan(len);
             S.sst[lane] = vs;
@@ -137,7 +140,8 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
     const int nh = counters[CNT_AGG_HEAVY];
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
         const int u = heavy[h];
-        const int s = g.split[u], e = g.nrow[u + 1], dp = e - s;
+        const int4 ru = g.rinfo[u];
+        const int s = ru.y, e = ru.z, dp = e - s;
         if (threadIdx.x == 0) any_tri = 0;
         __syncthreads();
         if (edge_aggregates(g, tcnt, vacc, u, s, dp, threadIdx.x, AC_THREADS) && lane == 0) any_tri = 1;
@@ -166,9 +170,9 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
             const int j = jb + lane;
             int len = 0, vs = 0;
             if (j < dp - 1 && tcnt[s + j] > 0) {
-                const int v = g.ncol[s + j];
-                vs = g.split[v];
-                len = g.nrow[v + 1] - vs;
+                const int4 rv = g.rinfo[g.ncol[s + j]];
+                vs = rv.y;
+                len = rv.z - rv.y;
             }
             const int incl = warp_inclusive_scan(len);
             sst[lane] = vs;
@@ -214,7 +218,7 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
 }
 
 void launch_stage2(Work &w, cudaStream_t st) {
-    Graph g{w.n, w.m, w.nrow, w.ncol, w.split};
+    Graph g{w.n, w.m, w.rinfo, w.ncol};
     int *heavy = w.lists + (size_t)w.n;
     const int maxd = w.tune[TUNE_WARP_MAXD] < AW_MAXD ? w.tune[TUNE_WARP_MAXD] : AW_MAXD;
     k_agg_warp<<<w.num_sms * w.tune[TUNE_GRID_AGG], AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters,

@@ -100,36 +100,6 @@ def test_repeated_calls_identical(ni):
         assert np.array_equal(gpu_count(ni, rp, ci), a)
 
 
-def _full_size_check(ni, rp, ci, nsample, seed):
-    """Invariants over all rows, then oracle rows for a sample: random
-    vertices, the 40 largest vertices of degree <= 5000 (their pair loops
-    stay affordable for the oracle) and 40 neighbours of the largest hub."""
-    got = gpu_count(ni, rp, ci)
-    assert cheap_sum_checks(rp, got) == []
-    d = np.diff(rp)
-    rng = np.random.default_rng(seed)
-    pick = set(rng.choice(len(d), size=nsample, replace=False).tolist())
-    order = np.argsort(-d, kind="stable")
-    pick.update(int(v) for v in order[d[order] <= 5000][:40])
-    top = int(order[0])
-    nb = ci[rp[top]:rp[top + 1]]
-    pick.update(int(v) for v in rng.choice(nb, size=min(40, len(nb)), replace=False))
-    verts = np.array(sorted(pick), dtype=np.int32)
-    exp = oracle.count_vertices(rp, ci, verts)
-    assert_same(got[verts], exp, "sampled rows")
-    return got
-
-
-def test_er_1e6_sampled(ni):
-    rp, ci = gg.er_mean_degree(1_000_000, 32, 1)
-    _full_size_check(ni, rp, ci, 300, 11)
-
-
-def test_rmat22_sampled(ni):
-    rp, ci = gg.rmat(22, 16, seed=1)
-    _full_size_check(ni, rp, ci, 200, 12)
-
-
 def test_batch_equals_single(ni):
     graphs = [gg.chunglu(int(n), 2.5, 8.0, 100 + i) for i, n in enumerate([50, 3, 1, 700, 2500, 90, 1200])]
     graphs.append(gg.complete(30))

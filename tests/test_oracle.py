@@ -114,7 +114,7 @@ def test_paper_form_equals_definition(name, g):
     assert np.array_equal(a.sum(axis=0), orbit_sums_expected(graphlet_totals(rp, ci)))
 
 
-@pytest.mark.parametrize("name,g", list(_medium_graphs())[:3])
+@pytest.mark.parametrize("name,g", list(_medium_graphs())[:3] + [("rmat11_hubs", gg.rmat(11, 16, seed=13))])
 def test_per_vertex_modes_equal_full(name, g):
     rp, ci = g
     n = len(rp) - 1
