@@ -47,12 +47,17 @@ def deg_class(d: np.ndarray) -> np.ndarray:
     return c
 
 
-def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray) -> dict:
-    """Per-stage algorithmic byte counts (int32 = 4 B) in the relabel order.
+def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 768, warp_maxd: int = 64) -> dict:
+    """Algorithmic byte counts (int32 = 4 B) in the relabel order, per stage
+    and per kernel tier.
 
     B_tri = 4 * sum over oriented edges (u, v) of min(d+u, d+v)
     B_c4  = 4 * number of wedges u - v - w with v, w below u (cycle roots)
     B_csr = 4 (n + 1) + 4 m, B_out = 120 n.
+    A root's wedges (or triangle probes) count for the tier kernel that
+    takes it: 4-cycle roots by the bound sum over in-neighbours of (d_v - 1)
+    (warp <= 768, mid <= 3072, cta <= 12288, else global), triangle roots by
+    out-degree (warp <= 64, else cta).
     """
     n = len(rowptr) - 1
     m = len(colidx)
@@ -60,20 +65,40 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray) -> dict:
     order = np.lexsort((np.arange(n), deg_class(d)))
     rank = np.empty(n, np.int64)
     rank[order] = np.arange(n)
+    dr = np.empty(n, np.int64)
+    dr[rank] = d                                   # degree by new id
     src = np.repeat(np.arange(n), d)
     rs, rd = rank[src], rank[colidx.astype(np.int64)]
     out = rd > rs
     dplus = np.bincount(rs[out], minlength=n)
-    b_tri = 4 * int(np.minimum(dplus[rs[out]], dplus[rd[out]]).sum())
+    probes = np.minimum(dplus[rs[out]], dplus[rd[out]])
+    tri_root = rs[out]
+    b_tri = 4 * int(probes.sum())
+    b_tri_cta = 4 * int(probes[dplus[tri_root] > warp_maxd].sum())
     # wedges rooted at u through in-neighbour v: entries of row v below u
     o2 = np.lexsort((rd, rs))
     rs2, rd2 = rs[o2], rd[o2]
     start = np.zeros(n + 1, np.int64)
     start[1:] = np.cumsum(np.bincount(rs2, minlength=n))
     pos = np.arange(m) - start[rs2]
-    w_c4 = int(pos[rd2 > rs2].sum())
-    return {"B_csr": 4 * (n + 1) + 4 * m, "B_tri": b_tri, "B_c4": 4 * w_c4, "W_c4": w_c4,
-            "B_out": 120 * n, "tri_probes": b_tri // 4}
+    sel = rd2 > rs2                                # entry (v -> u), u > v: pos wedges below u
+    w_root = np.bincount(rd2[sel], weights=pos[sel], minlength=n)
+    ub_root = np.bincount(rd2[sel], weights=dr[rs2[sel]] - 1, minlength=n)
+    din = np.bincount(rd2[sel], minlength=n)
+    live = din >= 2
+    tiers = {"k_c4_warp": live & (ub_root <= c4_warp_ub),
+             "k_c4_mid": live & (ub_root > c4_warp_ub) & (ub_root <= 3072),
+             "k_c4_cta": live & (ub_root > 3072) & (ub_root <= 12288),
+             "k_c4_global": live & (ub_root > 12288)}
+    w_c4 = int(w_root.sum())
+    res = {"B_csr": 4 * (n + 1) + 4 * m, "B_tri": b_tri, "B_c4": 4 * w_c4, "W_c4": w_c4, "B_out": 120 * n,
+           "tri_probes": b_tri // 4}
+    per_kernel = {"k_tri_warp": b_tri - b_tri_cta, "k_tri_cta": b_tri_cta,
+                  "k_relabel_rows_warp": 2 * res["B_csr"], "k_solve": res["B_csr"] + res["B_out"]}
+    for k, msk in tiers.items():
+        per_kernel[k] = 4 * int(w_root[msk].sum())
+    res["per_kernel"] = per_kernel
+    return res
 
 
 class ClockSampler:
@@ -290,12 +315,11 @@ def run_ours(args) -> None:
             torch.distributed.destroy_process_group()
         return
 
-    ab = algorithmic_bytes(rp, ci)
+    tun = ni.get_tuning()
+    ab = algorithmic_bytes(rp, ci, tun["c4_warp_maxw"], tun["warp_maxd"])
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs")
-    kernel_bytes = {"k_tri_warp": ab["B_tri"], "k_c4_warp": ab["B_c4"],
-                    "k_relabel_rows_warp": 2 * ab["B_csr"], "k_solve": ab["B_csr"] + ab["B_out"]}
-    alg = kernel_bytes.get(top_name)
+    alg = ab["per_kernel"].get(top_name)
     achieved = alg / (top_avg_ms * 1e-3) / 1e9 if alg else None
     roofline = {
         "bound": "hbm", "kernel": top_name, "achieved": achieved,

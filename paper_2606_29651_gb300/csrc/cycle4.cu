@@ -10,21 +10,26 @@
 // then
 //   u gets sum_w C(c_w, 2), w gets C(c_w, 2),
 //   each middle vertex v gets sum over its wedges of (c_w - 1).
-// With rows sorted, the wedges through v are the prefix of row v below u,
-// cut by a binary search for u. Tiers by wedge count W(u): one warp with a
-// 1024-slot shared table; one CTA with a 16384-slot shared table; one CTA
-// with a dense count row in global memory for the largest roots.
+// The wedges through v are the entries of row v below u; the whole row is
+// streamed (it is read anyway) and filtered, so there is no dependent search.
+// Roots are routed by the bound UB = sum over v of (d_v - 1) >= wedges:
+// one warp with a 1024-slot shared table, four warps with 4096 slots, a
+// 512-thread CTA with 16384 slots, or a CTA with a dense count row in global
+// memory. Each table is emptied once per CTA; afterwards a root empties only
+// the slots it filled (kept in a `touched` list).
 #include "kernels.h"
 
 namespace niorca {
 
-constexpr int CW_WARPS = 4;   // 4 x 11 KB of static shared memory
+constexpr int CW_WARPS = 4;
 constexpr int CW_SLOTS = 1024;
-constexpr int CW_MAXW = CW_SLOTS / 2;
+constexpr int CW_MAXUB = 768;
+constexpr int CM_THREADS = 128;
+constexpr int CM_SLOTS = 4096;
+constexpr int CM_MAXUB = 3072;
 constexpr int CC_THREADS = 512;
 constexpr int CC_SLOTS = 16384;
-constexpr int CC_MAXW = CC_SLOTS / 2;
-constexpr size_t CC_SMEM = (size_t)CC_SLOTS * 8 + (size_t)(CC_THREADS / 32) * 128 * 4;
+constexpr int CC_MAXUB = 12288;
 constexpr int CG_THREADS = 1024;
 
 __device__ __forceinline__ int seg_owner3(const int *pre, int k) {
@@ -38,21 +43,13 @@ __device__ __forceinline__ int seg_owner3(const int *pre, int k) {
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
-// Wedges through in-neighbour v of root u: row v from its start up to the
-// position of u, which lies in v's out-part [rv.y, rv.z).
-__device__ __forceinline__ int wedge_len(const Graph &g, int v, int u) {
-    const int4 rv = g.rinfo[v];
-    return lower_bound(g.ncol, rv.y, rv.z, u) - rv.x;
-}
-
-// Walks the wedges of root u: for every chunk of 32 in-neighbours (starting
-// at chunk `c0`, step `cstep` chunks), sets up the segment table of the warp
-// and calls f(q, pos) for each wedge (q: lane that owns v, pos: position of w),
-// then done(v, seg_len) once per chunk after a __syncwarp. `lens`, when not
-// null, holds the segment length of the first `nlens` in-neighbours.
+// Walks the wedges of root u (in-neighbours b .. b + din of row u): for every
+// chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...) the rows of those v
+// are concatenated across the warp; f(q, w) is called for each entry w < u
+// (q: lane that owns v), then done(v) once per chunk.
 template <class F, class D>
 __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep, int *sst,
-                                            int *spre, F f, D done, const int *lens = nullptr, int nlens = 0) {
+                                            int *spre, F f, D done) {
     const int lane = lane_id();
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
         const int p = cb + lane;
@@ -61,7 +58,7 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
             v = g.ncol[b + p];
             const int4 rv = g.rinfo[v];
             st = rv.x;
-            len = p < nlens ? lens[p] : lower_bound(g.ncol, rv.y, rv.z, u) - rv.x;
+            len = rv.z - rv.x;
         }
         const int incl = warp_inclusive_scan(len);
         sst[lane] = st;
@@ -72,26 +69,14 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
             const int k = kb + lane;
             if (k >= total) break;
             const int q = seg_owner3(spre, k);
-            f(q, sst[q] + (k - spre[q]));
+            const int w = g.ncol[sst[q] + (k - spre[q])];
+            if (w < u) f(q, w);
         }
         __syncwarp();
-        done(v, len);
+        done(v);
         __syncwarp();
     }
 }
-
-constexpr int CW_LENS = 64;   // cached wedge-segment lengths per root
-
-struct C4WarpSmem {
-    int hk[CW_SLOTS];      // keys (-1 = empty); all empty between roots
-    int hc[CW_SLOTS];      // wedge counts per key
-    int touched[CW_MAXW];  // slots filled by the current root
-    int lens[CW_LENS];
-    int sst[32];
-    int spre[32];
-    long long pv[32];
-    int ntouched;
-};
 
 // Counts `key`; returns the slot when this call inserted it, else -1.
 __device__ __forceinline__ int hcount_add_new(int *keys, int *cnts, unsigned mask, int key) {
@@ -109,132 +94,159 @@ __device__ __forceinline__ int hcount_add_new(int *keys, int *cnts, unsigned mas
     return -1;
 }
 
-// One warp per root with at most CW_MAXW wedges. The table is cleared once
-// per warp; afterwards every root empties only the slots it filled.
+// Shared-memory view of one root's table (keys, counts, filled slots).
+struct C4Tab {
+    int *hk, *hc, *touched, *ntouched;
+    unsigned mask;
+};
+
+// Counts all wedges of u into the table and credits every 4-cycle rooted at
+// u. Every thread of the group calls it; `sync` separates the passes; warp
+// `wid` of `nw` takes in-neighbour chunks wid, wid + nw, ...
+template <class Sync>
+__device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din, const C4Tab &T, int wid,
+                                        int nw, int tid, int nthreads, int *sst, int *spre, long long *pv,
+                                        int *any_cycle, Sync sync) {
+    const int lane = lane_id();
+    walk_wedges(g, u, b, din, wid, nw, sst, spre,
+                [&](int, int w) {
+                    const int slot = hcount_add_new(T.hk, T.hc, T.mask, w);
+                    if (slot >= 0) T.touched[atomicAdd(T.ntouched, 1)] = slot;
+                },
+                [&](int) {});
+    sync();
+    const int nt = *T.ntouched;
+    long long su = 0;
+    for (int i = tid; i < nt; i += nthreads) {
+        const int slot = T.touched[i];
+        const int c = T.hc[slot];
+        if (c >= 2) {
+            su += c2(c);
+            add64(&vacc[T.hk[slot]].C4, c2(c));
+        }
+    }
+    su = warp_sum(su);
+    if (lane == 0 && su) {
+        add64(&vacc[u].C4, su);
+        *any_cycle = 1;
+    }
+    sync();
+    if (*any_cycle) {   // middle vertices, only when some cycle is rooted at u
+        pv[lane] = 0;
+        __syncwarp();
+        walk_wedges(g, u, b, din, wid, nw, sst, spre,
+                    [&](int q, int w) {
+                        const int c = hcount_get(T.hk, T.hc, T.mask, w);
+                        if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
+                    },
+                    [&](int v) {
+                        const long long x = pv[lane];
+                        if (x) add64(&vacc[v].C4, x);
+                        pv[lane] = 0;
+                    });
+    }
+    sync();
+    for (int i = tid; i < nt; i += nthreads) {
+        const int slot = T.touched[i];
+        T.hk[slot] = -1;
+        T.hc[slot] = 0;
+    }
+    sync();
+    if (tid == 0) {
+        *T.ntouched = 0;
+        *any_cycle = 0;
+    }
+    sync();
+}
+
+struct C4WarpSmem {
+    int hk[CW_SLOTS];
+    int hc[CW_SLOTS];
+    int touched[CW_MAXUB];
+    int sst[32];
+    int spre[32];
+    long long pv[32];
+    int ntouched;
+    int any_cycle;
+};
+
+// One warp per root with UB <= maxub (<= CW_MAXUB); larger roots are queued.
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters,
-                                                           int maxw) {
+                                                           int maxub) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    int *cta_list = lists + 2 * (size_t)g.n;
-    int *glob_list = lists + 3 * (size_t)g.n;
-    constexpr unsigned mask = CW_SLOTS - 1;
+    int *mid_list = lists + 2 * (size_t)g.n;
+    int *cta_list = lists + 3 * (size_t)g.n;
+    int *glob_list = lists + 4 * (size_t)g.n;
     for (int i = lane; i < CW_SLOTS; i += 32) { S.hk[i] = -1; S.hc[i] = 0; }
-    if (lane == 0) S.ntouched = 0;
+    if (lane == 0) { S.ntouched = 0; S.any_cycle = 0; }
     __syncwarp();
+    const C4Tab T{S.hk, S.hc, S.touched, &S.ntouched, CW_SLOTS - 1};
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
         if (din < 2) continue;
-        long long W = 0;
+        long long ub = 0;
         for (int p = lane; p < din; p += 32) {
-            const int len = wedge_len(g, g.ncol[b + p], u);
-            if (p < CW_LENS) S.lens[p] = len;
-            W += len;
+            const int4 rv = g.rinfo[g.ncol[b + p]];
+            ub += rv.z - rv.x - 1;
         }
-        W = warp_sum(W);
-        if (W < 2) continue;
-        if (W > maxw) {
+        ub = warp_sum(ub);
+        if (ub < 2) continue;
+        if (ub > maxub) {
             if (lane == 0) {
-                if (W > CC_MAXW) glob_list[atomicAdd(&counters[CNT_C4_GLOBAL], 1)] = u;
-                else cta_list[atomicAdd(&counters[CNT_C4_CTA], 1)] = u;
+                if (ub > CC_MAXUB) glob_list[atomicAdd(&counters[CNT_C4_GLOBAL], 1)] = u;
+                else if (ub > CM_MAXUB) cta_list[atomicAdd(&counters[CNT_C4_CTA], 1)] = u;
+                else mid_list[atomicAdd(&counters[CNT_C4_MID], 1)] = u;
             }
             continue;
         }
-        __syncwarp();
-        walk_wedges(
-            g, u, b, din, 0, 1, S.sst, S.spre,
-            [&](int, int pos) {
-                const int slot = hcount_add_new(S.hk, S.hc, mask, g.ncol[pos]);
-                if (slot >= 0) S.touched[atomicAdd(&S.ntouched, 1)] = slot;
-            },
-            [&](int, int) {}, S.lens, CW_LENS);
-        const int nt = S.ntouched;
-        long long su = 0;
-        for (int i = lane; i < nt; i += 32) {
-            const int slot = S.touched[i];
-            const int c = S.hc[slot];
-            if (c >= 2) {
-                su += c2(c);
-                add64(&vacc[S.hk[slot]].C4, c2(c));
-            }
-        }
-        su = warp_sum(su);
-        if (lane == 0 && su) add64(&vacc[u].C4, su);
-        if (su) {   // middle vertices, only when some cycle is rooted at u
-            S.pv[lane] = 0;
-            __syncwarp();
-            walk_wedges(
-                g, u, b, din, 0, 1, S.sst, S.spre,
-                [&](int q, int pos) {
-                    const int c = hcount_get(S.hk, S.hc, mask, g.ncol[pos]);
-                    if (c > 1) atomicAdd((unsigned long long *)&S.pv[q], (unsigned long long)(c - 1));
-                },
-                [&](int v, int) {
-                    const long long x = S.pv[lane];
-                    if (x) add64(&vacc[v].C4, x);
-                    S.pv[lane] = 0;
-                },
-                S.lens, CW_LENS);
-        }
-        for (int i = lane; i < nt; i += 32) {
-            const int slot = S.touched[i];
-            S.hk[slot] = -1;
-            S.hc[slot] = 0;
-        }
-        __syncwarp();
-        if (lane == 0) S.ntouched = 0;
-        __syncwarp();
+        c4_root(g, vacc, u, b, din, T, 0, 1, lane, 32, S.sst, S.spre, S.pv, &S.any_cycle, [] { __syncwarp(); });
     }
 }
 
-// One CTA per root with CW_MAXW < W <= CC_MAXW: the table in shared memory.
-__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists, const int *counters) {
+// Roots from a queue, one CTA each, table of SLOTS entries in dynamic
+// shared memory (emptied once per CTA).
+template <int THREADS, int SLOTS, int MAXUB>
+__device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    constexpr int NW = CC_THREADS / 32;
+    constexpr int NW = THREADS / 32;
     int *hk = reinterpret_cast<int *>(dsm);
-    int *hc = hk + CC_SLOTS;
-    const int wid = threadIdx.x >> 5, lane = lane_id();
-    int *sst = hc + CC_SLOTS + wid * 128;
+    int *hc = hk + SLOTS;
+    int *touched = hc + SLOTS;
+    int *segs = touched + MAXUB;       // NW x 128 ints: sst, spre, pv (64-bit)
+    int *flags = segs + NW * 128;      // ntouched, any_cycle
+    const int wid = threadIdx.x >> 5;
+    int *sst = segs + wid * 128;
     int *spre = sst + 32;
     long long *pv = reinterpret_cast<long long *>(spre + 32);
-    const int *cta_list = lists + 2 * (size_t)g.n;
-    const int nh = counters[CNT_C4_CTA];
-    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int u = cta_list[h];
+    for (int i = threadIdx.x; i < SLOTS; i += THREADS) { hk[i] = -1; hc[i] = 0; }
+    if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; }
+    __syncthreads();
+    const C4Tab T{hk, hc, touched, &flags[0], SLOTS - 1};
+    for (int h = blockIdx.x; h < count; h += gridDim.x) {
+        const int u = list[h];
         const int4 ru = g.rinfo[u];
-        const int b = ru.x, din = ru.y - ru.x;
-        for (int i = threadIdx.x; i < CC_SLOTS; i += CC_THREADS) { hk[i] = -1; hc[i] = 0; }
-        pv[lane] = 0;
-        __syncthreads();
-        const unsigned mask = CC_SLOTS - 1;
-        walk_wedges(g, u, b, din, wid, NW, sst, spre,
-                    [&](int, int pos) { hcount_add(hk, hc, mask, g.ncol[pos]); }, [&](int, int) {});
-        __syncthreads();
-        long long su = 0;
-        for (int i = threadIdx.x; i < CC_SLOTS; i += CC_THREADS) {
-            const int c = hc[i];
-            if (c >= 2) {
-                su += c2(c);
-                add64(&vacc[hk[i]].C4, c2(c));
-            }
-        }
-        su = warp_sum(su);
-        if (lane == 0 && su) add64(&vacc[u].C4, su);
-        walk_wedges(g, u, b, din, wid, NW, sst, spre,
-                    [&](int q, int pos) {
-                        const int c = hcount_get(hk, hc, mask, g.ncol[pos]);
-                        if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
-                    },
-                    [&](int v, int) {
-                        const long long x = pv[lane];
-                        if (x) add64(&vacc[v].C4, x);
-                        pv[lane] = 0;
-                    });
-        __syncthreads();
+        c4_root(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1],
+                [] { __syncthreads(); });
     }
+}
+
+constexpr size_t cq_smem(int threads, int slots, int maxub) {
+    return (size_t)(2 * slots + maxub + (threads / 32) * 128 + 4) * 4;
+}
+constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXUB);
+constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXUB);
+
+__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists, const int *counters) {
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID]);
+}
+
+__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists, const int *counters) {
+    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA]);
 }
 
 // Zero the dense rows of the global tier (only when that tier has work).
@@ -252,8 +264,10 @@ __global__ void k_c4_zero_dense(int *dense, long long n, int slots, const int *c
         dense[i] = 0;
 }
 
-// One CTA per root with W > CC_MAXW: counts in a dense global row of n ints,
-// which the third pass returns to zero.
+// One CTA per root with UB > CC_MAXUB: counts in a dense global row of n ints.
+// Pass 1 adds every wedge; pass 2 reads each count (per middle vertex) and
+// marks the key with the sign bit, so that exactly one visitor credits
+// C(c, 2) to w; pass 3 stores zeros back.
 __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, const int *lists, const int *counters,
                                                           int *dense, int slots) {
     constexpr int NW = CG_THREADS / 32;
@@ -263,50 +277,47 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
     const int wid = threadIdx.x >> 5, lane = lane_id();
     int *sst = segs[wid], *spre = sst + 32;
     long long *pv = reinterpret_cast<long long *>(spre + 32);
-    const int *glob_list = lists + 3 * (size_t)g.n;
+    const int *glob_list = lists + 4 * (size_t)g.n;
     const int nh = counters[CNT_C4_GLOBAL];
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
         const int u = glob_list[h];
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
         pv[lane] = 0;
-        walk_wedges(g, u, b, din, wid, NW, sst, spre, [&](int, int pos) { atomicAdd(&row[g.ncol[pos]], 1); },
-                    [&](int, int) {});
-        __syncthreads();
-        walk_wedges(g, u, b, din, wid, NW, sst, spre,
-                    [&](int q, int pos) {
-                        const int c = __ldcg(&row[g.ncol[pos]]);   // counts were added at L2
-                        if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
-                    },
-                    [&](int v, int) {
-                        const long long x = pv[lane];
-                        if (x) add64(&vacc[v].C4, x);
-                        pv[lane] = 0;
-                    });
+        walk_wedges(g, u, b, din, wid, NW, sst, spre, [&](int, int w) { atomicAdd(&row[w], 1); }, [&](int) {});
         __syncthreads();
         long long su = 0;
         walk_wedges(g, u, b, din, wid, NW, sst, spre,
-                    [&](int, int pos) {
-                        const int w = g.ncol[pos];
-                        const int c = atomicExch(&row[w], 0);
-                        if (c >= 2) {
+                    [&](int q, int w) {
+                        const int old = atomicOr(&row[w], (int)0x80000000);
+                        const int c = old & 0x7fffffff;
+                        if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
+                        if (old >= 0 && c >= 2) {   // first visitor of this key
                             su += c2(c);
                             add64(&vacc[w].C4, c2(c));
                         }
                     },
-                    [&](int, int) {});
+                    [&](int v) {
+                        const long long x = pv[lane];
+                        if (x) add64(&vacc[v].C4, x);
+                        pv[lane] = 0;
+                    });
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
+        __syncthreads();
+        walk_wedges(g, u, b, din, wid, NW, sst, spre, [&](int, int w) { row[w] = 0; }, [&](int) {});
         __syncthreads();
     }
 }
 
 void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
-    const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
-    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw);
+    const int maxub = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXUB ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXUB;
+    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxub);
     after_launch(st, K_C4_WARP);
-    k_c4_cta<<<w.num_sms * 2, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters);
+    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters);
+    after_launch(st, K_C4_MID);
+    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters);
     after_launch(st, K_C4_CTA);
     if (w.c4slots > 0) {
         k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, w.n, w.c4slots, w.counters);
@@ -317,6 +328,7 @@ void launch_cycle4(Work &w, cudaStream_t st) {
 }
 
 void configure_cycle4() {
+    cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM);
 }
 
