@@ -120,6 +120,35 @@ niorca_status niorca_validate(const int32_t *rowptr, const int32_t *colidx, int3
  */
 niorca_status niorca_last_status(void *stream);
 
+/*
+ * Orbit counts of one graph without allocating any memory. The paper has no
+ * counterpart: this exists for callers that must not allocate device memory
+ * or let a library do so -- code whose device memory is owned and budgeted
+ * by a host application or framework (a plugin in another program's CUDA
+ * context, a runtime that hands out only its own buffers), or a system that
+ * forbids allocation once it is running. The counts are those of
+ * niorca_count.
+ *   rowptr, colidx, n, m, out, stream  as niorca_count
+ *   status  device int32 or NULL. The call sets it to 0, then ORs in bit k
+ *           for every device-detected error with code k (same codes as the
+ *           return value). With NULL such errors are not reported.
+ * Work memory: one static device array of NIORCA_NOALLOC_SCRATCH_BYTES
+ * (64 MiB) inside the library, which every GPU that loads the library holds
+ * until the process exits. A graph whose work memory does not fit (roughly
+ * 130 n + 8 m bytes, e.g. n = 1e5 with m = 4e6) is rejected with
+ * NIORCA_ENOMEM before anything is enqueued. The call uses the default
+ * launch shape, not niorca_set_tuning's.
+ * The first call on a device finds the array's device address (set-up, no
+ * allocation); make that first call before any stream capture. Every call
+ * on a device shares the one array: calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race and give wrong counts;
+ * calls on one stream, or otherwise ordered, are fine. The array keeps the
+ * last call's contents; each call clears what must start at zero.
+ */
+#define NIORCA_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+niorca_status niorca_count_noalloc(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                                   int64_t *out, int32_t *status, void *stream);
+
 /* Bytes of work memory one niorca_count call of this size takes. */
 size_t niorca_workspace_bytes(int32_t n, int64_t m);
 
