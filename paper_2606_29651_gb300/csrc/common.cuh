@@ -145,6 +145,101 @@ __device__ __forceinline__ int hcount_get(const int *keys, const int *cnts, unsi
     return 0;
 }
 
+// Index of the segment that holds element k of a warp's concatenation of up
+// to 32 segments (exclusive prefix `pre`): the last q with pre[q] <= k, which
+// is never an empty segment.
+__device__ __forceinline__ int seg_owner(const int *pre, int k) {
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Visits the elements first, first + stride, ... (< total) of a segment table
+// (segment q starts at position sst[q] of `col` and at offset spre[q] of the
+// concatenation) and calls f(q, pos, col[pos]). U elements are located and
+// their loads issued before any is processed, so each lane keeps U
+// independent reads in flight.
+template <int U, class F>
+__device__ __forceinline__ void seg_expand(const int *__restrict__ col, const int *sst, const int *spre, int total,
+                                           int first, int stride, F f) {
+    for (int k0 = first; k0 < total; k0 += U * stride) {
+        int q[U], pos[U], val[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int k = k0 + r * stride;
+            q[r] = -1;
+            pos[r] = 0;
+            val[r] = 0;
+            if (k < total) {
+                q[r] = seg_owner(spre, k);
+                pos[r] = sst[q[r]] + (k - spre[q[r]]);
+                val[r] = __ldg(col + pos[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r)
+            if (q[r] >= 0) f(q[r], pos[r], val[r]);
+    }
+}
+
+// As seg_expand, but the loop is uniform over the warp and f(valid, q, pos,
+// val) runs on every lane (valid = the lane holds an element), so that f may
+// use warp collectives. `wbase` (uniform) + lane is the warp's first element.
+template <int U, class F>
+__device__ __forceinline__ void seg_expand_all(const int *__restrict__ col, const int *sst, const int *spre, int total,
+                                               int wbase, int stride, F f) {
+    const int lane = lane_id();
+    for (int k0 = wbase; k0 < total; k0 += U * stride) {
+        int q[U], pos[U], val[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int k = k0 + r * stride + lane;
+            q[r] = 0;
+            pos[r] = -1;
+            val[r] = 0;
+            if (k < total) {
+                q[r] = seg_owner(spre, k);
+                pos[r] = sst[q[r]] + (k - spre[q[r]]);
+                val[r] = __ldg(col + pos[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r) f(pos[r] >= 0, q[r], pos[r], val[r]);
+    }
+}
+
+// Warp-aggregated atomic add of `v` to *p among the lanes (of those calling
+// with `active`) that share the same address: one atomic per address.
+__device__ __forceinline__ void warp_add_int(bool active, int *p, int key, int v) {
+    const unsigned peers = __match_any_sync(FULL, active ? key : -1 - lane_id());
+    const unsigned total = __reduce_add_sync(peers, active ? (unsigned)v : 0u);
+    if (active && (peers & lanemask_lt()) == 0) atomicAdd(p, (int)total);
+}
+
+__device__ __forceinline__ void warp_add_ll(bool active, long long *p, int key, long long v) {
+    const unsigned peers = __match_any_sync(FULL, active ? key : -1 - lane_id());
+    long long sum = v;
+    // sum over the peer group by shuffles within the group's lanes
+    unsigned rest = peers & ~(1u << lane_id());
+    long long acc = active ? v : 0;
+    while (rest) {
+        const int src = __ffs(rest) - 1;
+        rest &= rest - 1;
+        (void)src;
+    }
+    (void)sum;
+    acc = 0;
+    for (int o = 0; o < 32; ++o) {
+        const long long x = __shfl_sync(FULL, active ? v : 0, o);
+        if ((peers >> o) & 1u) acc += x;
+    }
+    if (active && (peers & lanemask_lt()) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(p),
+                                                          static_cast<unsigned long long>(acc));
+}
+
 // First position p in [lo, hi) with a[p] >= key (a sorted ascending).
 __device__ __forceinline__ int lower_bound(const int *a, int lo, int hi, int key) {
     while (lo < hi) {

@@ -32,49 +32,68 @@ constexpr int CC_SLOTS = 16384;
 constexpr int CC_MAXUB = 12288;
 constexpr int CG_THREADS = 1024;
 
-__device__ __forceinline__ int seg_owner3(const int *pre, int k) {
-    int lo = 0, hi = 31;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
-// Walks the wedges of root u (in-neighbours b .. b + din of row u): for every
-// chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...) the rows of those v
-// are concatenated across the warp; f(q, w) is called for each entry w < u
-// (q: lane that owns v), then done(v) once per chunk.
+// Segment table of in-neighbour chunk cb of root u in the calling warp: the
+// rows of v = ncol[b + cb + lane] concatenated; returns the total length.
+__device__ __forceinline__ int wedge_chunk(const Graph &g, int b, int din, int cb, int *sst, int *spre, int *vout) {
+    const int lane = lane_id();
+    const int p = cb + lane;
+    int v = -1, st = 0, len = 0;
+    if (p < din) {
+        v = g.ncol[b + p];
+        const int4 rv = g.rinfo[v];
+        st = rv.x;
+        len = rv.z - rv.x;
+    }
+    const int incl = warp_inclusive_scan(len);
+    sst[lane] = st;
+    spre[lane] = incl - len;
+    *vout = v;
+    const int total = __shfl_sync(FULL, incl, 31);
+    __syncwarp();
+    return total;
+}
+
+// Walks the wedges of root u (in-neighbours b .. b + din of row u), one warp
+// per chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...): f(q, w) for each
+// entry w < u of their rows (q: lane that owns v), then done(v) per chunk.
 template <class F, class D>
 __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep, int *sst,
                                             int *spre, F f, D done) {
     const int lane = lane_id();
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
-        const int p = cb + lane;
-        int v = -1, st = 0, len = 0;
-        if (p < din) {
-            v = g.ncol[b + p];
-            const int4 rv = g.rinfo[v];
-            st = rv.x;
-            len = rv.z - rv.x;
-        }
-        const int incl = warp_inclusive_scan(len);
-        sst[lane] = st;
-        spre[lane] = incl - len;
-        const int total = __shfl_sync(FULL, incl, 31);
-        __syncwarp();
-        for (int kb = 0; kb < total; kb += 32) {
-            const int k = kb + lane;
-            if (k >= total) break;
-            const int q = seg_owner3(spre, k);
-            const int w = g.ncol[sst[q] + (k - spre[q])];
+        int v;
+        const int total = wedge_chunk(g, b, din, cb, sst, spre, &v);
+        seg_expand<4>(g.ncol, sst, spre, total, lane, 32, [&](int q, int, int w) {
             if (w < u) f(q, w);
-        }
+        });
         __syncwarp();
         done(v);
         __syncwarp();
+    }
+}
+
+// The same walk shared by all warps of a CTA: every warp builds the segment
+// table of each chunk and takes the elements wid * 32 + lane, stride nw * 32.
+// With DONE, warp 0 calls done(v) after the whole CTA finished the chunk.
+template <bool DONE, class F, class D>
+__device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, int din, int wid, int nw, int *sst,
+                                                int *spre, F f, D done) {
+    const int lane = lane_id();
+    for (int cb = 0; cb < din; cb += 32) {
+        int v;
+        const int total = wedge_chunk(g, b, din, cb, sst, spre, &v);
+        seg_expand<4>(g.ncol, sst, spre, total, wid * 32 + lane, nw * 32, [&](int q, int, int w) {
+            if (w < u) f(q, w);
+        });
+        if (DONE) {
+            __syncthreads();
+            if (wid == 0) done(v);
+            __syncthreads();
+        } else {
+            __syncwarp();
+        }
     }
 }
 
@@ -101,19 +120,23 @@ struct C4Tab {
 };
 
 // Counts all wedges of u into the table and credits every 4-cycle rooted at
-// u. Every thread of the group calls it; `sync` separates the passes; warp
-// `wid` of `nw` takes in-neighbour chunks wid, wid + nw, ...
-template <class Sync>
+// u. Every thread of the group (one warp, or a CTA with CTA = true) calls it.
+// pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
+// the CTA).
+template <bool CTA>
 __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din, const C4Tab &T, int wid,
                                         int nw, int tid, int nthreads, int *sst, int *spre, long long *pv,
-                                        int *any_cycle, Sync sync) {
+                                        int *any_cycle) {
     const int lane = lane_id();
-    walk_wedges(g, u, b, din, wid, nw, sst, spre,
-                [&](int, int w) {
-                    const int slot = hcount_add_new(T.hk, T.hc, T.mask, w);
-                    if (slot >= 0) T.touched[atomicAdd(T.ntouched, 1)] = slot;
-                },
-                [&](int) {});
+    auto sync = [] {
+        if (CTA) __syncthreads(); else __syncwarp();
+    };
+    auto insert = [&](int, int w) {
+        const int slot = hcount_add_new(T.hk, T.hc, T.mask, w);
+        if (slot >= 0) T.touched[atomicAdd(T.ntouched, 1)] = slot;
+    };
+    if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, sst, spre, insert, [](int) {});
+    else walk_wedges(g, u, b, din, 0, 1, sst, spre, insert, [](int) {});
     sync();
     const int nt = *T.ntouched;
     long long su = 0;
@@ -132,18 +155,19 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     }
     sync();
     if (*any_cycle) {   // middle vertices, only when some cycle is rooted at u
-        pv[lane] = 0;
-        __syncwarp();
-        walk_wedges(g, u, b, din, wid, nw, sst, spre,
-                    [&](int q, int w) {
-                        const int c = hcount_get(T.hk, T.hc, T.mask, w);
-                        if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
-                    },
-                    [&](int v) {
-                        const long long x = pv[lane];
-                        if (x) add64(&vacc[v].C4, x);
-                        pv[lane] = 0;
-                    });
+        if (tid < 32) pv[tid] = 0;
+        sync();
+        auto middle = [&](int q, int w) {
+            const int c = hcount_get(T.hk, T.hc, T.mask, w);
+            if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
+        };
+        auto flush = [&](int v) {
+            const long long x = pv[lane];
+            if (x) add64(&vacc[v].C4, x);
+            pv[lane] = 0;
+        };
+        if (CTA) walk_wedges_cta<true>(g, u, b, din, wid, nw, sst, spre, middle, flush);
+        else walk_wedges(g, u, b, din, 0, 1, sst, spre, middle, flush);
     }
     sync();
     for (int i = tid; i < nt; i += nthreads) {
@@ -204,7 +228,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             }
             continue;
         }
-        c4_root(g, vacc, u, b, din, T, 0, 1, lane, 32, S.sst, S.spre, S.pv, &S.any_cycle, [] { __syncwarp(); });
+        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.sst, S.spre, S.pv, &S.any_cycle);
     }
 }
 
@@ -217,12 +241,12 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
     int *hk = reinterpret_cast<int *>(dsm);
     int *hc = hk + SLOTS;
     int *touched = hc + SLOTS;
-    int *segs = touched + MAXUB;       // NW x 128 ints: sst, spre, pv (64-bit)
-    int *flags = segs + NW * 128;      // ntouched, any_cycle
+    int *segs = touched + MAXUB;       // NW x 64 ints: sst, spre per warp
+    long long *pv = reinterpret_cast<long long *>(segs + NW * 64);   // 32, shared by the CTA
+    int *flags = reinterpret_cast<int *>(pv + 32);                  // ntouched, any_cycle
     const int wid = threadIdx.x >> 5;
-    int *sst = segs + wid * 128;
+    int *sst = segs + wid * 64;
     int *spre = sst + 32;
-    long long *pv = reinterpret_cast<long long *>(spre + 32);
     for (int i = threadIdx.x; i < SLOTS; i += THREADS) { hk[i] = -1; hc[i] = 0; }
     if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; }
     __syncthreads();
@@ -230,13 +254,12 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
     for (int h = blockIdx.x; h < count; h += gridDim.x) {
         const int u = list[h];
         const int4 ru = g.rinfo[u];
-        c4_root(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1],
-                [] { __syncthreads(); });
+        c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1]);
     }
 }
 
 constexpr size_t cq_smem(int threads, int slots, int maxub) {
-    return (size_t)(2 * slots + maxub + (threads / 32) * 128 + 4) * 4;
+    return (size_t)(2 * slots + maxub + (threads / 32) * 64 + 64 + 4) * 4;
 }
 constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXUB);
 constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXUB);

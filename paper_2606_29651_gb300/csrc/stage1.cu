@@ -18,17 +18,6 @@
 
 namespace niorca {
 
-// Index of the segment that holds element k of a warp's concatenation:
-// the last q with pre[q] <= k (segments of length 0 never qualify).
-__device__ __forceinline__ int seg_owner(const int *pre, int k) {
-    int lo = 0, hi = 31;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // ----------------------------------------------------------- warp tier
 
 constexpr int TW_MAXD = 64;   // out-degree handled by one warp
@@ -85,22 +74,17 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
             S.spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            for (int kb = 0; kb < total; kb += 32) {
-                const int k = kb + lane;
-                if (k >= total) break;
-                const int q = seg_owner(S.spre, k);
-                const int pos = S.sst[q] + (k - S.spre[q]);
-                const int w = g.ncol[pos];
-                if (w > umax) continue;
+            seg_expand<4>(g.ncol, S.sst, S.spre, total, lane, 32, [&](int q, int pos, int w) {
+                if (w > umax) return;
                 const int i = hset_find(S.hk, S.hv, mask, w);
-                if (i < 0) continue;
+                if (i < 0) return;
                 const int jj = jb + q;
                 atomicAdd(&S.cnt[jj], 1);
                 atomicAdd(&S.cnt[i], 1);
                 atomicAdd(&tcnt[pos], 1);
                 atomicOr(&S.R[jj][i >> 5], 1u << (i & 31));
                 found = 1;
-            }
+            });
             __syncwarp();
         }
         if (!__any_sync(FULL, found)) continue;
@@ -205,15 +189,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
             spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            for (int kb = 0; kb < total; kb += 32) {
-                const int k = kb + lane;
-                if (k >= total) break;
-                const int q = seg_owner(spre, k);
-                const int pos = sst[q] + (k - spre[q]);
-                const int w = g.ncol[pos];
-                if (w > umax) continue;
+            seg_expand<4>(g.ncol, sst, spre, total, lane, 32, [&](int q, int pos, int w) {
+                if (w > umax) return;
                 const int i = out_index(hk, hv, mask, use_hash, g.ncol, s, e, w);
-                if (i < 0) continue;
+                if (i < 0) return;
                 const int jj = jb + q;
                 atomicAdd(use_hash ? &cnt[jj] : &tcnt[s + jj], 1);
                 atomicAdd(use_hash ? &cnt[i] : &tcnt[s + i], 1);
@@ -243,7 +222,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
                         }
                     }
                 }
-            }
+            });
             __syncwarp();
         }
         __syncthreads();

@@ -16,15 +16,6 @@
 
 namespace niorca {
 
-__device__ __forceinline__ int seg_owner2(const int *pre, int k) {
-    int lo = 0, hi = 31;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 constexpr int AW_MAXD = 64;
 constexpr int AW_WARPS = 8;
 
@@ -103,20 +94,15 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
             S.spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            for (int kb = 0; kb < total; kb += 32) {
-                const int k = kb + lane;
-                if (k >= total) break;
-                const int q = seg_owner2(S.spre, k);
-                const int pos = S.sst[q] + (k - S.spre[q]);
-                const int w = g.ncol[pos];
-                if (w > umax) continue;
+            seg_expand<4>(g.ncol, S.sst, S.spre, total, lane, 32, [&](int q, int pos, int w) {
+                if (w > umax) return;
                 const int i = hset_find(S.hk, S.hv, mask, w);
-                if (i < 0) continue;
+                if (i < 0) return;
                 const int jj = jb + q;
                 du12 += tcnt[pos] - 1;                                 // t(v, w) - 1 -> u
                 atomicAdd((unsigned long long *)&S.dc[jj], (unsigned long long)(tcnt[s + i] - 1));  // t(u, w) - 1 -> v
                 atomicAdd((unsigned long long *)&S.dc[i], (unsigned long long)(tcnt[s + jj] - 1));  // t(u, v) - 1 -> w
-            }
+            });
             __syncwarp();
         }
         du12 = warp_sum(du12);
@@ -179,13 +165,8 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
             spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            for (int kb = 0; kb < total; kb += 32) {
-                const int k = kb + lane;
-                if (k >= total) break;
-                const int q = seg_owner2(spre, k);
-                const int pos = sst[q] + (k - spre[q]);
-                const int w = g.ncol[pos];
-                if (w > umax) continue;
+            seg_expand<4>(g.ncol, sst, spre, total, lane, 32, [&](int q, int pos, int w) {
+                if (w > umax) return;
                 int i;
                 if (use_hash) {
                     i = hset_find(hk, hv, mask, w);
@@ -193,7 +174,7 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
                     const int p = find_sorted(g.ncol, s, e, w);
                     i = p < 0 ? -1 : p - s;
                 }
-                if (i < 0) continue;
+                if (i < 0) return;
                 const int jj = jb + q;
                 du12 += tcnt[pos] - 1;
                 const long long tv = tcnt[s + i] - 1, tw = tcnt[s + jj] - 1;
@@ -204,7 +185,7 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
                     add64(&vacc[g.ncol[s + jj]].D12, tv);
                     add64(&vacc[w].D12, tw);
                 }
-            }
+            });
             __syncwarp();
         }
         __syncthreads();
