@@ -47,7 +47,7 @@ def deg_class(d: np.ndarray) -> np.ndarray:
     return c
 
 
-def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 768, warp_maxd: int = 64) -> dict:
+def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 1536, warp_maxd: int = 64) -> dict:
     """Algorithmic byte counts (int32 = 4 B) in the relabel order, per stage
     and per kernel tier.
 
@@ -56,8 +56,9 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     B_csr = 4 (n + 1) + 4 m, B_out = 120 n.
     A root's wedges (or triangle probes) count for the tier kernel that
     takes it: 4-cycle roots by the bound sum over in-neighbours of (d_v - 1)
-    (warp <= 768, mid <= 3072, cta <= 12288, else global), triangle roots by
-    out-degree (warp <= 64, else cta).
+    (warp <= 1536 with a packed table, packed mid <= 6144, split mid <= 3072,
+    cta <= 12288, else global), triangle roots by out-degree (warp <= 64,
+    else cta).
     """
     n = len(rowptr) - 1
     m = len(colidx)
@@ -85,10 +86,13 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     w_root = np.bincount(rd2[sel], weights=pos[sel], minlength=n)
     ub_root = np.bincount(rd2[sel], weights=dr[rs2[sel]] - 1, minlength=n)
     din = np.bincount(rd2[sel], minlength=n)
-    live = din >= 2
-    tiers = {"k_c4_warp": live & (ub_root <= c4_warp_ub),
-             "k_c4_mid": live & (ub_root > c4_warp_ub) & (ub_root <= 3072),
-             "k_c4_cta": live & (ub_root > 3072) & (ub_root <= 12288),
+    live = (din >= 2) & (ub_root >= 2)
+    pack_lim = (1 << (32 - int(n - 1).bit_length())) - 2     # packed tables hold counts below this
+    warp = live & (ub_root <= min(c4_warp_ub, pack_lim))
+    midp = live & ~warp & (ub_root <= 6144) & (ub_root <= pack_lim)
+    mid = live & ~warp & ~midp & (ub_root <= 3072)
+    cta = live & ~warp & ~midp & ~mid & (ub_root <= 12288)
+    tiers = {"k_c4_warp": warp, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
              "k_c4_global": live & (ub_root > 12288)}
     w_c4 = int(w_root.sum())
     res = {"B_csr": 4 * (n + 1) + 4 * m, "B_tri": b_tri, "B_c4": 4 * w_c4, "W_c4": w_c4, "B_out": 120 * n,

@@ -219,25 +219,13 @@ __device__ __forceinline__ void warp_add_int(bool active, int *p, int key, int v
     if (active && (peers & lanemask_lt()) == 0) atomicAdd(p, (int)total);
 }
 
-__device__ __forceinline__ void warp_add_ll(bool active, long long *p, int key, long long v) {
+// Same for a 64-bit counter; v >= 0 and below 2^26, so the sum over a warp
+// fits 32 bits (every t is at most the 2^20 degree bound).
+__device__ __forceinline__ void warp_add_ll(bool active, long long *p, int key, int v) {
     const unsigned peers = __match_any_sync(FULL, active ? key : -1 - lane_id());
-    long long sum = v;
-    // sum over the peer group by shuffles within the group's lanes
-    unsigned rest = peers & ~(1u << lane_id());
-    long long acc = active ? v : 0;
-    while (rest) {
-        const int src = __ffs(rest) - 1;
-        rest &= rest - 1;
-        (void)src;
-    }
-    (void)sum;
-    acc = 0;
-    for (int o = 0; o < 32; ++o) {
-        const long long x = __shfl_sync(FULL, active ? v : 0, o);
-        if ((peers >> o) & 1u) acc += x;
-    }
-    if (active && (peers & lanemask_lt()) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(p),
-                                                          static_cast<unsigned long long>(acc));
+    const unsigned total = __reduce_add_sync(peers, active ? (unsigned)v : 0u);
+    if (active && (peers & lanemask_lt()) == 0)
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(total));
 }
 
 // First position p in [lo, hi) with a[p] >= key (a sorted ascending).

@@ -12,25 +12,29 @@
 //   each middle vertex v gets sum over its wedges of (c_w - 1).
 // The wedges through v are the entries of row v below u; the whole row is
 // streamed (it is read anyway) and filtered, so there is no dependent search.
-// Roots are routed by the bound UB = sum over v of (d_v - 1) >= wedges:
-// one warp with a 1024-slot shared table, four warps with 4096 slots, a
-// 512-thread CTA with 16384 slots, or a CTA with a dense count row in global
-// memory. Each table is emptied once per CTA; afterwards a root empties only
-// the slots it filled (kept in a `touched` list).
+// Roots are routed by the bound UB = sum over v of (d_v - 1) >= wedges
+// (a count is at most UB too): one warp, four warps, a 512-thread CTA, or a
+// CTA with a dense count row in global memory. Tables are open-addressing
+// hash tables in shared memory, either split (key and count arrays) or
+// packed (key << cb | count in one 32-bit word, cb = 32 - bits(n - 1) count
+// bits, usable while UB < 2^cb - 1), which holds twice the keys in the same
+// space. Each table is emptied once per CTA; afterwards a root empties only
+// the slots it filled (kept in a 16-bit `touched` list).
 #include "kernels.h"
 
 namespace niorca {
 
 constexpr int CW_WARPS = 4;
-constexpr int CW_SLOTS = 1024;
-constexpr int CW_MAXUB = 768;
+constexpr int CW_SLOTS = 2048;      // packed
+constexpr int CW_MAXUB = 1536;
 constexpr int CM_THREADS = 128;
-constexpr int CM_SLOTS = 4096;
-constexpr int CM_MAXUB = 3072;
+constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
+constexpr int CM_MAXUB = 3072;      // split; 6144 when packed
 constexpr int CC_THREADS = 512;
-constexpr int CC_SLOTS = 16384;
+constexpr int CC_SLOTS = 16384;     // split
 constexpr int CC_MAXUB = 12288;
 constexpr int CG_THREADS = 1024;
+constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
@@ -97,34 +101,79 @@ __device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, in
     }
 }
 
-// Counts `key`; returns the slot when this call inserted it, else -1.
-__device__ __forceinline__ int hcount_add_new(int *keys, int *cnts, unsigned mask, int key) {
-    unsigned s = hash_slot(key, mask);
-    for (unsigned probe = 0; probe <= mask; ++probe) {
-        int k = keys[s];
-        if (k == -1) {
-            const int prev = atomicCAS(&keys[s], -1, key);
-            if (prev == -1) { atomicAdd(&cnts[s], 1); return (int)s; }
-            k = prev;
-        }
-        if (k == key) { atomicAdd(&cnts[s], 1); return -1; }
-        s = (s + 1) & mask;
-    }
-    return -1;
-}
-
-// Shared-memory view of one root's table (keys, counts, filled slots).
-struct C4Tab {
-    int *hk, *hc, *touched, *ntouched;
+// Split table: keys (-1 empty) and counts in two arrays.
+struct SplitTab {
+    int *hk, *hc;
     unsigned mask;
+    unsigned short *touched;
+    int *ntouched;
+    // counts w; returns the slot if this call inserted w, else -1
+    __device__ __forceinline__ int add(int w) const {
+        unsigned s = hash_slot(w, mask);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            int k = hk[s];
+            if (k == -1) {
+                const int prev = atomicCAS(&hk[s], -1, w);
+                if (prev == -1) { atomicAdd(&hc[s], 1); return (int)s; }
+                k = prev;
+            }
+            if (k == w) { atomicAdd(&hc[s], 1); return -1; }
+            s = (s + 1) & mask;
+        }
+        return -1;
+    }
+    __device__ __forceinline__ int get(int w) const { return hcount_get(hk, hc, mask, w); }
+    __device__ __forceinline__ int key(int s) const { return hk[s]; }
+    __device__ __forceinline__ int cnt(int s) const { return hc[s]; }
+    __device__ __forceinline__ void clear(int s) const { hk[s] = -1; hc[s] = 0; }
+};
+
+// Packed table: one word (w << cb) | count per slot, EMPTY when free. A
+// count never reaches 2^cb - 1 (the caller ensures UB < 2^cb - 1), so a full
+// word is never EMPTY.
+struct PackedTab {
+    unsigned *t;
+    unsigned mask;
+    int cb;
+    unsigned short *touched;
+    int *ntouched;
+    __device__ __forceinline__ int add(int w) const {
+        const unsigned key = static_cast<unsigned>(w);
+        unsigned s = hash_slot(w, mask);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            unsigned cur = t[s];
+            if (cur == EMPTY) {
+                const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
+                if (prev == EMPTY) return (int)s;
+                cur = prev;
+            }
+            if ((cur >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
+            s = (s + 1) & mask;
+        }
+        return -1;
+    }
+    __device__ __forceinline__ int get(int w) const {
+        const unsigned key = static_cast<unsigned>(w);
+        unsigned s = hash_slot(w, mask);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            const unsigned cur = t[s];
+            if (cur == EMPTY) return 0;
+            if ((cur >> cb) == key) return (int)(cur & ((1u << cb) - 1));
+            s = (s + 1) & mask;
+        }
+        return 0;
+    }
+    __device__ __forceinline__ int key(int s) const { return (int)(t[s] >> cb); }
+    __device__ __forceinline__ int cnt(int s) const { return (int)(t[s] & ((1u << cb) - 1)); }
+    __device__ __forceinline__ void clear(int s) const { t[s] = EMPTY; }
 };
 
 // Counts all wedges of u into the table and credits every 4-cycle rooted at
 // u. Every thread of the group (one warp, or a CTA with CTA = true) calls it.
 // pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
 // the CTA).
-template <bool CTA>
-__device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din, const C4Tab &T, int wid,
+template <bool CTA, class Tab>
+__device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din, const Tab &T, int wid,
                                         int nw, int tid, int nthreads, int *sst, int *spre, long long *pv,
                                         int *any_cycle) {
     const int lane = lane_id();
@@ -132,8 +181,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         if (CTA) __syncthreads(); else __syncwarp();
     };
     auto insert = [&](int, int w) {
-        const int slot = hcount_add_new(T.hk, T.hc, T.mask, w);
-        if (slot >= 0) T.touched[atomicAdd(T.ntouched, 1)] = slot;
+        const int slot = T.add(w);
+        if (slot >= 0) T.touched[atomicAdd(T.ntouched, 1)] = (unsigned short)slot;
     };
     if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, sst, spre, insert, [](int) {});
     else walk_wedges(g, u, b, din, 0, 1, sst, spre, insert, [](int) {});
@@ -142,10 +191,10 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     long long su = 0;
     for (int i = tid; i < nt; i += nthreads) {
         const int slot = T.touched[i];
-        const int c = T.hc[slot];
+        const int c = T.cnt(slot);
         if (c >= 2) {
             su += c2(c);
-            add64(&vacc[T.hk[slot]].C4, c2(c));
+            add64(&vacc[T.key(slot)].C4, c2(c));
         }
     }
     su = warp_sum(su);
@@ -158,7 +207,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         if (tid < 32) pv[tid] = 0;
         sync();
         auto middle = [&](int q, int w) {
-            const int c = hcount_get(T.hk, T.hc, T.mask, w);
+            const int c = T.get(w);
             if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
         };
         auto flush = [&](int v) {
@@ -170,11 +219,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         else walk_wedges(g, u, b, din, 0, 1, sst, spre, middle, flush);
     }
     sync();
-    for (int i = tid; i < nt; i += nthreads) {
-        const int slot = T.touched[i];
-        T.hk[slot] = -1;
-        T.hc[slot] = 0;
-    }
+    for (int i = tid; i < nt; i += nthreads) T.clear(T.touched[i]);
     sync();
     if (tid == 0) {
         *T.ntouched = 0;
@@ -184,9 +229,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
 }
 
 struct C4WarpSmem {
-    int hk[CW_SLOTS];
-    int hc[CW_SLOTS];
-    int touched[CW_MAXUB];
+    unsigned t[CW_SLOTS];
+    unsigned short touched[CW_MAXUB];
     int sst[32];
     int spre[32];
     long long pv[32];
@@ -194,21 +238,20 @@ struct C4WarpSmem {
     int any_cycle;
 };
 
-// One warp per root with UB <= maxub (<= CW_MAXUB); larger roots are queued.
+// One warp per root with UB <= maxub (<= CW_MAXUB) that fits a packed table;
+// other roots are queued for the wider tiers.
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters,
-                                                           int maxub) {
+                                                           int maxub, int cb) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    int *mid_list = lists + 2 * (size_t)g.n;
-    int *cta_list = lists + 3 * (size_t)g.n;
-    int *glob_list = lists + 4 * (size_t)g.n;
-    for (int i = lane; i < CW_SLOTS; i += 32) { S.hk[i] = -1; S.hc[i] = 0; }
+    const long long pack_lim = (1ll << cb) - 2;   // largest UB a packed count may reach
+    for (int i = lane; i < CW_SLOTS; i += 32) S.t[i] = EMPTY;
     if (lane == 0) { S.ntouched = 0; S.any_cycle = 0; }
     __syncwarp();
-    const C4Tab T{S.hk, S.hc, S.touched, &S.ntouched, CW_SLOTS - 1};
+    const PackedTab T{S.t, CW_SLOTS - 1, cb, S.touched, &S.ntouched};
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
@@ -220,11 +263,14 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
         }
         ub = warp_sum(ub);
         if (ub < 2) continue;
-        if (ub > maxub) {
+        if (ub > maxub || ub > pack_lim) {
             if (lane == 0) {
-                if (ub > CC_MAXUB) glob_list[atomicAdd(&counters[CNT_C4_GLOBAL], 1)] = u;
-                else if (ub > CM_MAXUB) cta_list[atomicAdd(&counters[CNT_C4_CTA], 1)] = u;
-                else mid_list[atomicAdd(&counters[CNT_C4_MID], 1)] = u;
+                int which, list;   // queue counter and list slot (lists + list * n)
+                if (ub > CC_MAXUB) { which = CNT_C4_GLOBAL; list = 4; }
+                else if (ub <= 2 * CM_MAXUB && ub <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
+                else if (ub <= CM_MAXUB) { which = CNT_C4_MID; list = 2; }
+                else { which = CNT_C4_CTA; list = 3; }
+                lists[(size_t)list * g.n + atomicAdd(&counters[which], 1)] = u;
             }
             continue;
         }
@@ -232,44 +278,63 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
     }
 }
 
-// Roots from a queue, one CTA each, table of SLOTS entries in dynamic
-// shared memory (emptied once per CTA).
-template <int THREADS, int SLOTS, int MAXUB>
-__device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count) {
+// Roots from a queue, one CTA each. The table (SLOTS split slots, or
+// 2 x SLOTS packed ones) lives in dynamic shared memory and is emptied once
+// per CTA.
+template <int THREADS, int SLOTS, int MAXUB, bool PACKED>
+__device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count, int cb) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
-    int *hk = reinterpret_cast<int *>(dsm);
-    int *hc = hk + SLOTS;
-    int *touched = hc + SLOTS;
-    int *segs = touched + MAXUB;       // NW x 64 ints: sst, spre per warp
-    long long *pv = reinterpret_cast<long long *>(segs + NW * 64);   // 32, shared by the CTA
+    constexpr int NT = PACKED ? 2 * MAXUB : MAXUB;   // touched capacity
+    unsigned *words = reinterpret_cast<unsigned *>(dsm);            // 2 x SLOTS words
+    unsigned short *touched = reinterpret_cast<unsigned short *>(words + 2 * SLOTS);
+    int *segs = reinterpret_cast<int *>(touched + NT);              // NW x 64 ints: sst, spre per warp
+    long long *pv = reinterpret_cast<long long *>(segs + NW * 64);  // 32, shared by the CTA
     int *flags = reinterpret_cast<int *>(pv + 32);                  // ntouched, any_cycle
     const int wid = threadIdx.x >> 5;
     int *sst = segs + wid * 64;
     int *spre = sst + 32;
-    for (int i = threadIdx.x; i < SLOTS; i += THREADS) { hk[i] = -1; hc[i] = 0; }
+    if (PACKED) {
+        for (int i = threadIdx.x; i < 2 * SLOTS; i += THREADS) words[i] = EMPTY;
+    } else {
+        for (int i = threadIdx.x; i < SLOTS; i += THREADS) { words[i] = EMPTY; words[SLOTS + i] = 0; }
+    }
     if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; }
     __syncthreads();
-    const C4Tab T{hk, hc, touched, &flags[0], SLOTS - 1};
     for (int h = blockIdx.x; h < count; h += gridDim.x) {
         const int u = list[h];
         const int4 ru = g.rinfo[u];
-        c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1]);
+        if (PACKED) {
+            const PackedTab T{words, 2 * SLOTS - 1, cb, touched, &flags[0]};
+            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1]);
+        } else {
+            const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS - 1,
+                             touched, &flags[0]};
+            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1]);
+        }
     }
 }
 
 constexpr size_t cq_smem(int threads, int slots, int maxub) {
-    return (size_t)(2 * slots + maxub + (threads / 32) * 64 + 64 + 4) * 4;
+    // 2 x slots words, 2 x maxub 16-bit touched entries, segments, pv, flags
+    return (size_t)2 * slots * 4 + (size_t)2 * maxub * 2 + (size_t)(threads / 32) * 64 * 4 + 32 * 8 + 16;
 }
 constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXUB);
 constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXUB);
 
-__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists, const int *counters) {
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID]);
+__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists, const int *counters,
+                                                       int cb) {
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
 }
 
-__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists, const int *counters) {
-    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA]);
+__global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, VAcc *vacc, const int *lists, const int *counters,
+                                                        int cb) {
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
+}
+
+__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists, const int *counters,
+                                                       int cb) {
+    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
 }
 
 // Zero the dense rows of the global tier (only when that tier has work).
@@ -333,14 +398,25 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
     }
 }
 
+// Count bits of a packed table for ids below n: the key takes bits(n - 1).
+static int packed_count_bits(int n) {
+    unsigned top = n > 1 ? (unsigned)(n - 1) : 1u;
+    int kb = 0;
+    while (top) { ++kb; top >>= 1; }
+    return 32 - kb;
+}
+
 void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxub = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXUB ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXUB;
-    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxub);
+    const int cb = packed_count_bits(w.n);
+    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxub, cb);
     after_launch(st, K_C4_WARP);
-    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters);
+    k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    after_launch(st, K_C4_MIDP);
+    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MID);
-    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters);
+    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
     if (w.c4slots > 0) {
         k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, w.n, w.c4slots, w.counters);
@@ -352,6 +428,7 @@ void launch_cycle4(Work &w, cudaStream_t st) {
 
 void configure_cycle4() {
     cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
+    cudaFuncSetAttribute(k_c4_midp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM);
 }
 

@@ -74,16 +74,22 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
             S.spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            seg_expand<4>(g.ncol, S.sst, S.spre, total, lane, 32, [&](int q, int pos, int w) {
-                if (w > umax) return;
-                const int i = hset_find(S.hk, S.hv, mask, w);
-                if (i < 0) return;
+            seg_expand_all<2>(g.ncol, S.sst, S.spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+                const int i = (valid && w <= umax) ? hset_find(S.hk, S.hv, mask, w) : -1;
+                const bool hit = i >= 0;
+                if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
-                atomicAdd(&S.cnt[jj], 1);
-                atomicAdd(&S.cnt[i], 1);
-                atomicAdd(&tcnt[pos], 1);
-                atomicOr(&S.R[jj][i >> 5], 1u << (i & 31));
-                found = 1;
+                // lanes of one segment share t(u, v) and words of R: one atomic each
+                warp_add_int(hit, &S.cnt[jj], jj, 1);
+                const int word = jj * 2 + (i >> 5);
+                const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
+                const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
+                if (hit) {
+                    if ((peers & lanemask_lt()) == 0) atomicOr(&S.R[0][0] + word, bits);
+                    atomicAdd(&S.cnt[i], 1);
+                    atomicAdd(&tcnt[pos], 1);
+                    found = 1;
+                }
             });
             __syncwarp();
         }
@@ -189,17 +195,22 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
             spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            seg_expand<4>(g.ncol, sst, spre, total, lane, 32, [&](int q, int pos, int w) {
-                if (w > umax) return;
-                const int i = out_index(hk, hv, mask, use_hash, g.ncol, s, e, w);
-                if (i < 0) return;
+            seg_expand_all<4>(g.ncol, sst, spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+                const int i = (valid && w <= umax) ? out_index(hk, hv, mask, use_hash, g.ncol, s, e, w) : -1;
+                const bool hit = i >= 0;
+                if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
-                atomicAdd(use_hash ? &cnt[jj] : &tcnt[s + jj], 1);
+                warp_add_int(hit, use_hash ? &cnt[jj] : &tcnt[s + jj], jj, 1);
+                if (use_bits) {
+                    const int word = jj * W + (i >> 5);
+                    const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
+                    const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
+                    if (hit && (peers & lanemask_lt()) == 0) atomicOr(&R[word], bits);
+                }
+                if (!hit) return;
                 atomicAdd(use_hash ? &cnt[i] : &tcnt[s + i], 1);
                 atomicAdd(&tcnt[pos], 1);
-                if (use_bits) {
-                    atomicOr(&R[jj * W + (i >> 5)], 1u << (i & 31));
-                } else {
+                if (!use_bits) {
                     // K4 with this triangle (u, v, w): x in N+(w) ∩ N+(u) ∩ N+(v)
                     const int v = g.ncol[s + jj];
                     const int4 rv = g.rinfo[v], rw = g.rinfo[w];

@@ -94,13 +94,14 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
             S.spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            seg_expand<4>(g.ncol, S.sst, S.spre, total, lane, 32, [&](int q, int pos, int w) {
-                if (w > umax) return;
-                const int i = hset_find(S.hk, S.hv, mask, w);
-                if (i < 0) return;
+            seg_expand_all<2>(g.ncol, S.sst, S.spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+                const int i = (valid && w <= umax) ? hset_find(S.hk, S.hv, mask, w) : -1;
+                const bool hit = i >= 0;
+                if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
-                du12 += tcnt[pos] - 1;                                 // t(v, w) - 1 -> u
-                atomicAdd((unsigned long long *)&S.dc[jj], (unsigned long long)(tcnt[s + i] - 1));  // t(u, w) - 1 -> v
+                warp_add_ll(hit, &S.dc[jj], jj, hit ? tcnt[s + i] - 1 : 0);   // t(u, w) - 1 -> v
+                if (!hit) return;
+                du12 += tcnt[pos] - 1;                                       // t(v, w) - 1 -> u
                 atomicAdd((unsigned long long *)&S.dc[i], (unsigned long long)(tcnt[s + jj] - 1));  // t(u, v) - 1 -> w
             });
             __syncwarp();
@@ -165,26 +166,26 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
             spre[lane] = incl - len;
             const int total = __shfl_sync(FULL, incl, 31);
             __syncwarp();
-            seg_expand<4>(g.ncol, sst, spre, total, lane, 32, [&](int q, int pos, int w) {
-                if (w > umax) return;
-                int i;
-                if (use_hash) {
-                    i = hset_find(hk, hv, mask, w);
-                } else {
-                    const int p = find_sorted(g.ncol, s, e, w);
-                    i = p < 0 ? -1 : p - s;
+            seg_expand_all<4>(g.ncol, sst, spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+                int i = -1;
+                if (valid && w <= umax) {
+                    if (use_hash) {
+                        i = hset_find(hk, hv, mask, w);
+                    } else {
+                        const int p = find_sorted(g.ncol, s, e, w);
+                        i = p < 0 ? -1 : p - s;
+                    }
                 }
-                if (i < 0) return;
+                const bool hit = i >= 0;
+                if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
+                const int tv = hit ? tcnt[s + i] - 1 : 0;
+                warp_add_ll(hit, use_hash ? &dc[jj] : &vacc[g.ncol[s + jj]].D12, jj, tv);
+                if (!hit) return;
                 du12 += tcnt[pos] - 1;
-                const long long tv = tcnt[s + i] - 1, tw = tcnt[s + jj] - 1;
-                if (use_hash) {
-                    atomicAdd((unsigned long long *)&dc[jj], (unsigned long long)tv);
-                    atomicAdd((unsigned long long *)&dc[i], (unsigned long long)tw);
-                } else {
-                    add64(&vacc[g.ncol[s + jj]].D12, tv);
-                    add64(&vacc[w].D12, tw);
-                }
+                const long long tw = tcnt[s + jj] - 1;
+                if (use_hash) atomicAdd((unsigned long long *)&dc[i], (unsigned long long)tw);
+                else add64(&vacc[w].D12, tw);
             });
             __syncwarp();
         }
