@@ -145,72 +145,6 @@ __device__ __forceinline__ int hcount_get(const int *keys, const int *cnts, unsi
     return 0;
 }
 
-// Index of the segment that holds element k of a warp's concatenation of up
-// to 32 segments (exclusive prefix `pre`): the last q with pre[q] <= k, which
-// is never an empty segment.
-__device__ __forceinline__ int seg_owner(const int *pre, int k) {
-    int lo = 0, hi = 31;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (pre[mid] <= k) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Visits the elements first, first + stride, ... (< total) of a segment table
-// (segment q starts at position sst[q] of `col` and at offset spre[q] of the
-// concatenation) and calls f(q, pos, col[pos]). U elements are located and
-// their loads issued before any is processed, so each lane keeps U
-// independent reads in flight.
-template <int U, class F>
-__device__ __forceinline__ void seg_expand(const int *__restrict__ col, const int *sst, const int *spre, int total,
-                                           int first, int stride, F f) {
-    for (int k0 = first; k0 < total; k0 += U * stride) {
-        int q[U], pos[U], val[U];
-#pragma unroll
-        for (int r = 0; r < U; ++r) {
-            const int k = k0 + r * stride;
-            q[r] = -1;
-            pos[r] = 0;
-            val[r] = 0;
-            if (k < total) {
-                q[r] = seg_owner(spre, k);
-                pos[r] = sst[q[r]] + (k - spre[q[r]]);
-                val[r] = __ldg(col + pos[r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < U; ++r)
-            if (q[r] >= 0) f(q[r], pos[r], val[r]);
-    }
-}
-
-// As seg_expand, but the loop is uniform over the warp and f(valid, q, pos,
-// val) runs on every lane (valid = the lane holds an element), so that f may
-// use warp collectives. `wbase` (uniform) + lane is the warp's first element.
-template <int U, class F>
-__device__ __forceinline__ void seg_expand_all(const int *__restrict__ col, const int *sst, const int *spre, int total,
-                                               int wbase, int stride, F f) {
-    const int lane = lane_id();
-    for (int k0 = wbase; k0 < total; k0 += U * stride) {
-        int q[U], pos[U], val[U];
-#pragma unroll
-        for (int r = 0; r < U; ++r) {
-            const int k = k0 + r * stride + lane;
-            q[r] = 0;
-            pos[r] = -1;
-            val[r] = 0;
-            if (k < total) {
-                q[r] = seg_owner(spre, k);
-                pos[r] = sst[q[r]] + (k - spre[q[r]]);
-                val[r] = __ldg(col + pos[r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < U; ++r) f(pos[r] >= 0, q[r], pos[r], val[r]);
-    }
-}
-
 // Warp-aggregated atomic add of `v` to *p among the lanes (of those calling
 // with `active`) that share the same address: one atomic per address.
 __device__ __forceinline__ void warp_add_int(bool active, int *p, int key, int v) {
@@ -226,6 +160,67 @@ __device__ __forceinline__ void warp_add_ll(bool active, long long *p, int key, 
     const unsigned total = __reduce_add_sync(peers, active ? (unsigned)v : 0u);
     if (active && (peers & lanemask_lt()) == 0)
         atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(total));
+}
+
+// Per-warp table of the segments of one chunk (one segment per lane, e.g. the
+// out-list of one neighbour), compacted to the non-empty ones in lane order:
+// st = start position in the column array, pre = offset in the concatenation,
+// idx = the lane that owns the segment.
+struct SegTab {
+    int st[32];
+    int pre[32];
+    int idx[32];
+};
+
+// Fills the table from each lane's segment (st, len); returns the length of
+// the concatenation and the lane's own offset in `mypre`.
+__device__ __forceinline__ int seg_build(SegTab &T, int st, int len, int &mypre) {
+    const int incl = warp_inclusive_scan(len);
+    mypre = incl - len;
+    const unsigned ne = __ballot_sync(FULL, len > 0);
+    if (len > 0) {
+        const int r = __popc(ne & lanemask_lt());
+        T.st[r] = st;
+        T.pre[r] = mypre;
+        T.idx[r] = lane_id();
+    }
+    __syncwarp();
+    return __shfl_sync(FULL, incl, 31);
+}
+
+// Visits the concatenation in windows of 32 elements starting at wbase,
+// wbase + stride, ... (wbase and stride warp-uniform multiples of 32), U
+// windows per round with their loads issued first. The segment of element
+// ws + lane is found without a search: one reduction marks where non-empty
+// segments start inside the window, one ballot counts those that start
+// before it. f(valid, q, pos, col[pos]) runs on every lane (q = owning lane).
+template <int U, class F>
+__device__ __forceinline__ void seg_visit(const int *__restrict__ col, const SegTab &T, int mypre, int mylen,
+                                          int total, int wbase, int stride, F f) {
+    const int lane = lane_id();
+    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    for (int w0 = wbase; w0 < total; w0 += U * stride) {
+        int q[U], pos[U], val[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const int ws = w0 + r * stride;
+            const bool starts = mylen > 0 && mypre >= ws && mypre < ws + 32;
+            const unsigned sb = __reduce_or_sync(FULL, starts ? (1u << (mypre - ws)) : 0u);
+            const int before = __popc(__ballot_sync(FULL, mylen > 0 && mypre < ws));
+            const int k = ws + lane;
+            q[r] = 0;
+            pos[r] = -1;
+            val[r] = 0;
+            if (k < total) {
+                const int rk = before + __popc(sb & le) - 1;
+                q[r] = T.idx[rk];
+                pos[r] = T.st[rk] + (k - T.pre[rk]);
+                val[r] = __ldg(col + pos[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r) f(pos[r] >= 0, q[r], pos[r], val[r]);
+    }
 }
 
 // First position p in [lo, hi) with a[p] >= key (a sorted ascending).

@@ -39,38 +39,34 @@ constexpr unsigned EMPTY = 0xffffffffu;
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
 // Segment table of in-neighbour chunk cb of root u in the calling warp: the
-// rows of v = ncol[b + cb + lane] concatenated; returns the total length.
-__device__ __forceinline__ int wedge_chunk(const Graph &g, int b, int din, int cb, int *sst, int *spre, int *vout) {
-    const int lane = lane_id();
-    const int p = cb + lane;
-    int v = -1, st = 0, len = 0;
+// rows of v = ncol[b + cb + lane] concatenated. Returns the total length; the
+// lane's own v, segment length and offset come back in v, len, pre.
+__device__ __forceinline__ int wedge_chunk(const Graph &g, int b, int din, int cb, SegTab &T, int &v, int &len,
+                                           int &pre) {
+    const int p = cb + lane_id();
+    int st = 0;
+    v = -1;
+    len = 0;
     if (p < din) {
         v = g.ncol[b + p];
         const int4 rv = g.rinfo[v];
         st = rv.x;
         len = rv.z - rv.x;
     }
-    const int incl = warp_inclusive_scan(len);
-    sst[lane] = st;
-    spre[lane] = incl - len;
-    *vout = v;
-    const int total = __shfl_sync(FULL, incl, 31);
-    __syncwarp();
-    return total;
+    return seg_build(T, st, len, pre);
 }
 
 // Walks the wedges of root u (in-neighbours b .. b + din of row u), one warp
 // per chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...): f(q, w) for each
 // entry w < u of their rows (q: lane that owns v), then done(v) per chunk.
 template <class F, class D>
-__device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep, int *sst,
-                                            int *spre, F f, D done) {
-    const int lane = lane_id();
+__device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep, SegTab &T, F f,
+                                            D done) {
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
-        int v;
-        const int total = wedge_chunk(g, b, din, cb, sst, spre, &v);
-        seg_expand<4>(g.ncol, sst, spre, total, lane, 32, [&](int q, int, int w) {
-            if (w < u) f(q, w);
+        int v, len, pre;
+        const int total = wedge_chunk(g, b, din, cb, T, v, len, pre);
+        seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) {
+            if (ok && w < u) f(q, w);
         });
         __syncwarp();
         done(v);
@@ -79,17 +75,16 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
 }
 
 // The same walk shared by all warps of a CTA: every warp builds the segment
-// table of each chunk and takes the elements wid * 32 + lane, stride nw * 32.
-// With DONE, warp 0 calls done(v) after the whole CTA finished the chunk.
+// table of each chunk and takes the windows wid, wid + nw, ... of 32
+// elements. With DONE, warp 0 calls done(v) after the CTA finished the chunk.
 template <bool DONE, class F, class D>
-__device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, int din, int wid, int nw, int *sst,
-                                                int *spre, F f, D done) {
-    const int lane = lane_id();
+__device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, int din, int wid, int nw, SegTab &T,
+                                                F f, D done) {
     for (int cb = 0; cb < din; cb += 32) {
-        int v;
-        const int total = wedge_chunk(g, b, din, cb, sst, spre, &v);
-        seg_expand<4>(g.ncol, sst, spre, total, wid * 32 + lane, nw * 32, [&](int q, int, int w) {
-            if (w < u) f(q, w);
+        int v, len, pre;
+        const int total = wedge_chunk(g, b, din, cb, T, v, len, pre);
+        seg_visit<4>(g.ncol, T, pre, len, total, wid * 32, nw * 32, [&](bool ok, int q, int, int w) {
+            if (ok && w < u) f(q, w);
         });
         if (DONE) {
             __syncthreads();
@@ -174,8 +169,7 @@ struct PackedTab {
 // the CTA).
 template <bool CTA, class Tab>
 __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din, const Tab &T, int wid,
-                                        int nw, int tid, int nthreads, int *sst, int *spre, long long *pv,
-                                        int *any_cycle) {
+                                        int nw, int tid, int nthreads, SegTab &seg, long long *pv, int *any_cycle) {
     const int lane = lane_id();
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
@@ -184,8 +178,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         const int slot = T.add(w);
         if (slot >= 0) T.touched[atomicAdd(T.ntouched, 1)] = (unsigned short)slot;
     };
-    if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, sst, spre, insert, [](int) {});
-    else walk_wedges(g, u, b, din, 0, 1, sst, spre, insert, [](int) {});
+    if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
+    else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {});
     sync();
     const int nt = *T.ntouched;
     long long su = 0;
@@ -215,8 +209,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
             if (x) add64(&vacc[v].C4, x);
             pv[lane] = 0;
         };
-        if (CTA) walk_wedges_cta<true>(g, u, b, din, wid, nw, sst, spre, middle, flush);
-        else walk_wedges(g, u, b, din, 0, 1, sst, spre, middle, flush);
+        if (CTA) walk_wedges_cta<true>(g, u, b, din, wid, nw, seg, middle, flush);
+        else walk_wedges(g, u, b, din, 0, 1, seg, middle, flush);
     }
     sync();
     for (int i = tid; i < nt; i += nthreads) T.clear(T.touched[i]);
@@ -231,8 +225,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
 struct C4WarpSmem {
     unsigned t[CW_SLOTS];
     unsigned short touched[CW_MAXUB];
-    int sst[32];
-    int spre[32];
+    SegTab seg;
     long long pv[32];
     int ntouched;
     int any_cycle;
@@ -274,7 +267,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             }
             continue;
         }
-        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.sst, S.spre, S.pv, &S.any_cycle);
+        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, &S.any_cycle);
     }
 }
 
@@ -288,12 +281,11 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
     constexpr int NT = PACKED ? 2 * MAXUB : MAXUB;   // touched capacity
     unsigned *words = reinterpret_cast<unsigned *>(dsm);            // 2 x SLOTS words
     unsigned short *touched = reinterpret_cast<unsigned short *>(words + 2 * SLOTS);
-    int *segs = reinterpret_cast<int *>(touched + NT);              // NW x 64 ints: sst, spre per warp
-    long long *pv = reinterpret_cast<long long *>(segs + NW * 64);  // 32, shared by the CTA
+    SegTab *segs = reinterpret_cast<SegTab *>(touched + NT);         // one per warp
+    long long *pv = reinterpret_cast<long long *>(segs + NW);        // 32, shared by the CTA
     int *flags = reinterpret_cast<int *>(pv + 32);                  // ntouched, any_cycle
     const int wid = threadIdx.x >> 5;
-    int *sst = segs + wid * 64;
-    int *spre = sst + 32;
+    SegTab &seg = segs[wid];
     if (PACKED) {
         for (int i = threadIdx.x; i < 2 * SLOTS; i += THREADS) words[i] = EMPTY;
     } else {
@@ -306,18 +298,18 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
         const int4 ru = g.rinfo[u];
         if (PACKED) {
             const PackedTab T{words, 2 * SLOTS - 1, cb, touched, &flags[0]};
-            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1]);
+            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
         } else {
             const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS - 1,
                              touched, &flags[0]};
-            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, sst, spre, pv, &flags[1]);
+            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
         }
     }
 }
 
 constexpr size_t cq_smem(int threads, int slots, int maxub) {
     // 2 x slots words, 2 x maxub 16-bit touched entries, segments, pv, flags
-    return (size_t)2 * slots * 4 + (size_t)2 * maxub * 2 + (size_t)(threads / 32) * 64 * 4 + 32 * 8 + 16;
+    return (size_t)2 * slots * 4 + (size_t)2 * maxub * 2 + (size_t)(threads / 32) * sizeof(SegTab) + 32 * 8 + 16;
 }
 constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXUB);
 constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXUB);
@@ -359,12 +351,13 @@ __global__ void k_c4_zero_dense(int *dense, long long n, int slots, const int *c
 __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, const int *lists, const int *counters,
                                                           int *dense, int slots) {
     constexpr int NW = CG_THREADS / 32;
-    __shared__ __align__(8) int segs[NW][128];
+    __shared__ SegTab segs[NW];
+    __shared__ long long pvs[NW][32];
     if ((int)blockIdx.x >= slots) return;
     int *row = dense + (size_t)blockIdx.x * g.n;
     const int wid = threadIdx.x >> 5, lane = lane_id();
-    int *sst = segs[wid], *spre = sst + 32;
-    long long *pv = reinterpret_cast<long long *>(spre + 32);
+    SegTab &seg = segs[wid];
+    long long *pv = pvs[wid];
     const int *glob_list = lists + 4 * (size_t)g.n;
     const int nh = counters[CNT_C4_GLOBAL];
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
@@ -372,10 +365,10 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
         pv[lane] = 0;
-        walk_wedges(g, u, b, din, wid, NW, sst, spre, [&](int, int w) { atomicAdd(&row[w], 1); }, [&](int) {});
+        walk_wedges(g, u, b, din, wid, NW, seg, [&](int, int w) { atomicAdd(&row[w], 1); }, [&](int) {});
         __syncthreads();
         long long su = 0;
-        walk_wedges(g, u, b, din, wid, NW, sst, spre,
+        walk_wedges(g, u, b, din, wid, NW, seg,
                     [&](int q, int w) {
                         const int old = atomicOr(&row[w], (int)0x80000000);
                         const int c = old & 0x7fffffff;
@@ -393,7 +386,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
         __syncthreads();
-        walk_wedges(g, u, b, din, wid, NW, sst, spre, [&](int, int w) { row[w] = 0; }, [&](int) {});
+        walk_wedges(g, u, b, din, wid, NW, seg, [&](int, int w) { row[w] = 0; }, [&](int) {});
         __syncthreads();
     }
 }

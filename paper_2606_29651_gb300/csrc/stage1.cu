@@ -29,8 +29,7 @@ struct TriWarpSmem {
     int cnt[TW_MAXD];
     int kc[TW_MAXD];
     unsigned R[TW_MAXD][2];
-    int sst[32];
-    int spre[32];
+    SegTab seg;
 };
 
 __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, VAcc *vacc, int *heavy,
@@ -69,12 +68,9 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
                 vs = rv.y;
                 len = rv.z - rv.y;
             }
-            const int incl = warp_inclusive_scan(len);
-            S.sst[lane] = vs;
-            S.spre[lane] = incl - len;
-            const int total = __shfl_sync(FULL, incl, 31);
-            __syncwarp();
-            seg_expand_all<2>(g.ncol, S.sst, S.spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            int mypre;
+            const int total = seg_build(S.seg, vs, len, mypre);
+            seg_visit<2>(g.ncol, S.seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? hset_find(S.hk, S.hv, mask, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
@@ -132,11 +128,11 @@ constexpr int TC_HASH_MAXD = 8192;     // beyond this, membership is a binary se
 constexpr size_t TC_SMEM = (size_t)2 * 2048 * 4          // hash keys + values (dp <= 1024)
                            + (size_t)2 * TC_BITMAT_MAXD * 4  // cnt + kc
                            + (size_t)TC_BITMAT_MAXD * (TC_BITMAT_MAXD / 32) * 4  // R
-                           + (size_t)(TC_THREADS / 32) * 64 * 4;                 // per-warp segments
+                           + (size_t)(TC_THREADS / 32) * sizeof(SegTab);         // per-warp segments
 // Same budget re-cut for TC_BITMAT_MAXD < dp <= TC_HASH_MAXD: a 16384-slot
 // hash (128 KB) + cnt/kc (64 KB) + segments; checked on the host.
 constexpr size_t TC_SMEM_HASHONLY = (size_t)2 * 16384 * 4 + (size_t)2 * TC_HASH_MAXD * 4 +
-                                    (size_t)(TC_THREADS / 32) * 64 * 4;
+                                    (size_t)(TC_THREADS / 32) * sizeof(SegTab);
 constexpr size_t TC_SMEM_MAX = TC_SMEM > TC_SMEM_HASHONLY ? TC_SMEM : TC_SMEM_HASHONLY;
 
 __device__ __forceinline__ int out_index(const int *hk, const int *hv, unsigned mask, bool use_hash, const int *ncol,
@@ -168,10 +164,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
         int *hv = hk + H;
         int *cnt = hv + H;
         int *kc = cnt + nloc;
-        int *segs = kc + nloc;            // NW x 64 ints
-        unsigned *R = reinterpret_cast<unsigned *>(segs + NW * 64);
-        int *sst = segs + wid * 64;
-        int *spre = sst + 32;
+        SegTab *segs = reinterpret_cast<SegTab *>(kc + nloc);   // one per warp
+        unsigned *R = reinterpret_cast<unsigned *>(segs + NW);
+        SegTab &seg = segs[wid];
         for (int i = threadIdx.x; i < (int)H; i += TC_THREADS) hk[i] = -1;
         for (int i = threadIdx.x; i < nloc; i += TC_THREADS) { cnt[i] = 0; kc[i] = 0; }
         if (use_bits)
@@ -190,12 +185,9 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
                 vs = rv.y;
                 len = rv.z - rv.y;
             }
-            const int incl = warp_inclusive_scan(len);
-            sst[lane] = vs;
-            spre[lane] = incl - len;
-            const int total = __shfl_sync(FULL, incl, 31);
-            __syncwarp();
-            seg_expand_all<4>(g.ncol, sst, spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            int mypre;
+            const int total = seg_build(seg, vs, len, mypre);
+            seg_visit<4>(g.ncol, seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? out_index(hk, hv, mask, use_hash, g.ncol, s, e, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;

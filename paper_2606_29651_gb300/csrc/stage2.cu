@@ -23,8 +23,7 @@ struct AggWarpSmem {
     int hk[2 * AW_MAXD];
     int hv[2 * AW_MAXD];
     long long dc[AW_MAXD];
-    int sst[32];
-    int spre[32];
+    SegTab seg;
 };
 
 // Edge aggregates of u's out-edges; returns whether any has a triangle.
@@ -89,12 +88,9 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
                 vs = rv.y;
                 len = rv.z - rv.y;
             }
-            const int incl = warp_inclusive_scan(len);
-            S.sst[lane] = vs;
-            S.spre[lane] = incl - len;
-            const int total = __shfl_sync(FULL, incl, 31);
-            __syncwarp();
-            seg_expand_all<2>(g.ncol, S.sst, S.spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            int mypre;
+            const int total = seg_build(S.seg, vs, len, mypre);
+            seg_visit<2>(g.ncol, S.seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? hset_find(S.hk, S.hv, mask, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
@@ -116,7 +112,7 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
 
 constexpr int AC_THREADS = 256;
 constexpr int AC_HASH_MAXD = 8192;
-constexpr size_t AC_SMEM = (size_t)2 * 16384 * 4 + (size_t)AC_HASH_MAXD * 8 + (size_t)(AC_THREADS / 32) * 64 * 4;
+constexpr size_t AC_SMEM = (size_t)2 * 16384 * 4 + (size_t)AC_HASH_MAXD * 8 + (size_t)(AC_THREADS / 32) * sizeof(SegTab);
 
 __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
                                                         const int *counters) {
@@ -140,9 +136,7 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
         long long *dc = reinterpret_cast<long long *>(dsm);      // dp (only with the hash)
         int *hk = reinterpret_cast<int *>(dc + (use_hash ? dp : 0));
         int *hv = hk + H;
-        int *segs = hv + H;
-        int *sst = segs + wid * 64;
-        int *spre = sst + 32;
+        SegTab &seg = reinterpret_cast<SegTab *>(hv + H)[wid];
         if (use_hash) {
             for (int i = threadIdx.x; i < (int)H; i += AC_THREADS) hk[i] = -1;
             for (int i = threadIdx.x; i < dp; i += AC_THREADS) dc[i] = 0;
@@ -161,12 +155,9 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
                 vs = rv.y;
                 len = rv.z - rv.y;
             }
-            const int incl = warp_inclusive_scan(len);
-            sst[lane] = vs;
-            spre[lane] = incl - len;
-            const int total = __shfl_sync(FULL, incl, 31);
-            __syncwarp();
-            seg_expand_all<4>(g.ncol, sst, spre, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            int mypre;
+            const int total = seg_build(seg, vs, len, mypre);
+            seg_visit<4>(g.ncol, seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
                 int i = -1;
                 if (valid && w <= umax) {
                     if (use_hash) {
