@@ -368,8 +368,8 @@ def run_single_config(args) -> None:
         rp, ci = gg.er(2000, 0.01, 1)
         desc = "Erdos-Renyi G(n=2000, p=0.01), seed 1"
     else:
-        rp, ci = gg.rmat(22, 16, seed=1)
-        desc = "R-MAT scale 22, edge factor 16, (.57,.19,.19,.05), seed 1"
+        rp, ci = gg.rmat(args.rmat_scale, 16, seed=1)
+        desc = f"R-MAT scale {args.rmat_scale}, edge factor 16, (.57,.19,.19,.05), seed 1"
     edges = len(ci) // 2
     d_rp, d_ci = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
     out = torch.empty((len(rp) - 1, 15), dtype=torch.int64, device=dev)
@@ -530,6 +530,7 @@ def main() -> None:
     ap.add_argument("--workload", choices=["er1e6", "er2000", "rmat22", "batch", "serve"], default="er1e6",
                     help="er1e6 is the headline line; the others print their own records")
     ap.add_argument("--batch-graphs", type=int, default=8192)
+    ap.add_argument("--rmat-scale", type=int, default=22)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-max-edges", type=float, default=5e6)
     ap.add_argument("--serve-budget-gb", type=int, default=32)

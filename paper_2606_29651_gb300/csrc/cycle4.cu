@@ -57,17 +57,16 @@ __device__ __forceinline__ int wedge_chunk(const Graph &g, int b, int din, int c
 }
 
 // Walks the wedges of root u (in-neighbours b .. b + din of row u), one warp
-// per chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...): f(q, w) for each
-// entry w < u of their rows (q: lane that owns v), then done(v) per chunk.
+// per chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...): f(act, q, w) on
+// every lane, act meaning that w is an entry below u of the row of the v
+// owned by lane q; then done(v) per chunk.
 template <class F, class D>
 __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep, SegTab &T, F f,
                                             D done) {
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
         int v, len, pre;
         const int total = wedge_chunk(g, b, din, cb, T, v, len, pre);
-        seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) {
-            if (ok && w < u) f(q, w);
-        });
+        seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok && w < u, q, w); });
         __syncwarp();
         done(v);
         __syncwarp();
@@ -83,9 +82,8 @@ __device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, in
     for (int cb = 0; cb < din; cb += 32) {
         int v, len, pre;
         const int total = wedge_chunk(g, b, din, cb, T, v, len, pre);
-        seg_visit<4>(g.ncol, T, pre, len, total, wid * 32, nw * 32, [&](bool ok, int q, int, int w) {
-            if (ok && w < u) f(q, w);
-        });
+        seg_visit<4>(g.ncol, T, pre, len, total, wid * 32, nw * 32,
+                     [&](bool ok, int q, int, int w) { f(ok && w < u, q, w); });
         if (DONE) {
             __syncthreads();
             if (wid == 0) done(v);
@@ -174,9 +172,15 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
     };
-    auto insert = [&](int, int w) {
-        const int slot = T.add(w);
-        if (slot >= 0) T.touched[atomicAdd(T.ntouched, 1)] = (unsigned short)slot;
+    auto insert = [&](bool act, int, int w) {
+        const int slot = act ? T.add(w) : -1;
+        // new keys of the warp take consecutive `touched` entries: one atomic
+        const unsigned fresh = __ballot_sync(FULL, slot >= 0);
+        if (!fresh) return;
+        int base = 0;
+        if (lane == __ffs(fresh) - 1) base = atomicAdd(T.ntouched, __popc(fresh));
+        base = __shfl_sync(FULL, base, __ffs(fresh) - 1);
+        if (slot >= 0) T.touched[base + __popc(fresh & lanemask_lt())] = (unsigned short)slot;
     };
     if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
     else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {});
@@ -200,7 +204,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     if (*any_cycle) {   // middle vertices, only when some cycle is rooted at u
         if (tid < 32) pv[tid] = 0;
         sync();
-        auto middle = [&](int q, int w) {
+        auto middle = [&](bool act, int q, int w) {
+            if (!act) return;
             const int c = T.get(w);
             if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
         };
@@ -365,11 +370,13 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
         pv[lane] = 0;
-        walk_wedges(g, u, b, din, wid, NW, seg, [&](int, int w) { atomicAdd(&row[w], 1); }, [&](int) {});
+        walk_wedges(g, u, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); },
+                    [&](int) {});
         __syncthreads();
         long long su = 0;
         walk_wedges(g, u, b, din, wid, NW, seg,
-                    [&](int q, int w) {
+                    [&](bool act, int q, int w) {
+                        if (!act) return;
                         const int old = atomicOr(&row[w], (int)0x80000000);
                         const int c = old & 0x7fffffff;
                         if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
@@ -386,7 +393,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
         __syncthreads();
-        walk_wedges(g, u, b, din, wid, NW, seg, [&](int, int w) { row[w] = 0; }, [&](int) {});
+        walk_wedges(g, u, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) row[w] = 0; }, [&](int) {});
         __syncthreads();
     }
 }
