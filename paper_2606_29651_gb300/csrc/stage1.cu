@@ -13,7 +13,10 @@
 // R[j] bit i <=> N+(u)[i] in N+(N+(u)[j]). A K4 u < v < w < x is then a
 // triangle (j, i) of R together with a common bit of R[j] and R[i], so the
 // K4 count of each triangle is popc(R[j] & R[i]) -- Algorithm 2's pairwise
-// test over `neigh` done as word-wide bit operations.
+// test over `neigh` done as word-wide bit operations. In the CTA tier the
+// fourth vertex x is credited through its column C[x] = {j : x in R[j]}:
+// sum over j in C[x] of popc(R[j] & C[x]), so the cost follows the edges of
+// R and not the (much larger) number of K4s of dense hub neighbourhoods.
 #include "kernels.h"
 
 namespace niorca {
@@ -128,11 +131,12 @@ constexpr int TC_HASH_MAXD = 8192;     // beyond this, membership is a binary se
 constexpr size_t TC_SMEM = (size_t)2 * 2048 * 4          // hash keys + values (dp <= 1024)
                            + (size_t)2 * TC_BITMAT_MAXD * 4  // cnt + kc
                            + (size_t)TC_BITMAT_MAXD * (TC_BITMAT_MAXD / 32) * 4  // R
-                           + (size_t)(TC_THREADS / 32) * sizeof(SegTab);         // per-warp segments
+                           + (size_t)(TC_THREADS / 32) * (sizeof(SegTab) + 128)  // segments, column words
+                           + 16;                                                 // work counters
 // Same budget re-cut for TC_BITMAT_MAXD < dp <= TC_HASH_MAXD: a 16384-slot
 // hash (128 KB) + cnt/kc (64 KB) + segments; checked on the host.
 constexpr size_t TC_SMEM_HASHONLY = (size_t)2 * 16384 * 4 + (size_t)2 * TC_HASH_MAXD * 4 +
-                                    (size_t)(TC_THREADS / 32) * sizeof(SegTab);
+                                    (size_t)(TC_THREADS / 32) * (sizeof(SegTab) + 128) + 16;
 constexpr size_t TC_SMEM_MAX = TC_SMEM > TC_SMEM_HASHONLY ? TC_SMEM : TC_SMEM_HASHONLY;
 
 __device__ __forceinline__ int out_index(const int *hk, const int *hv, unsigned mask, bool use_hash, const int *ncol,
@@ -165,19 +169,25 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
         int *cnt = hv + H;
         int *kc = cnt + nloc;
         SegTab *segs = reinterpret_cast<SegTab *>(kc + nloc);   // one per warp
-        unsigned *R = reinterpret_cast<unsigned *>(segs + NW);
+        unsigned *colbuf = reinterpret_cast<unsigned *>(segs + NW);  // NW x 32 column words
+        int *work = reinterpret_cast<int *>(colbuf + NW * 32);        // next row, next column
+        unsigned *R = reinterpret_cast<unsigned *>(work + 4);
         SegTab &seg = segs[wid];
         for (int i = threadIdx.x; i < (int)H; i += TC_THREADS) hk[i] = -1;
         for (int i = threadIdx.x; i < nloc; i += TC_THREADS) { cnt[i] = 0; kc[i] = 0; }
         if (use_bits)
             for (int i = threadIdx.x; i < dp * W; i += TC_THREADS) R[i] = 0;
+        if (threadIdx.x < 2) work[threadIdx.x] = 0;
         __syncthreads();
         if (use_hash)
             for (int i = threadIdx.x; i < dp; i += TC_THREADS) hset_insert(hk, hv, mask, g.ncol[s + i], i);
         const int umax = g.ncol[e - 1];
         __syncthreads();
         long long ku = 0;
-        for (int jb = wid * 32; jb < dp - 1; jb += NW * 32) {
+        // every warp takes every chunk of 32 out-neighbours and the windows
+        // wid, wid + NW, ... of its concatenated lists: no warp waits on a
+        // larger chunk of another
+        for (int jb = 0; jb < dp - 1; jb += 32) {
             const int j = jb + lane;
             int len = 0, vs = 0;
             if (j < dp - 1) {
@@ -187,7 +197,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
             }
             int mypre;
             const int total = seg_build(seg, vs, len, mypre);
-            seg_visit<4>(g.ncol, seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            seg_visit<4>(g.ncol, seg, mypre, len, total, wid * 32, NW * 32, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? out_index(hk, hv, mask, use_hash, g.ncol, s, e, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
@@ -232,26 +242,65 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
         for (int i = threadIdx.x; i < nloc; i += TC_THREADS)
             if (cnt[i]) atomicAdd(&tcnt[s + i], cnt[i]);
         if (use_bits) {
-            for (int j = threadIdx.x; j < dp; j += TC_THREADS) {
+            // Rows: a warp takes row j, its lanes the set bits i of R[j];
+            // popc(R[j] & R[i]) K4s have v_j second and w_i third.
+            for (;;) {
+                int j = 0;
+                if (lane == 0) j = atomicAdd(&work[0], 1);
+                j = __shfl_sync(FULL, j, 0);
+                if (j >= dp) break;
                 const unsigned *rj = R + j * W;
-                for (int wd = 0; wd < W; ++wd) {
-                    unsigned bits = rj[wd];
+                long long kj = 0;
+                for (int t = lane; t < W; t += 32) {
+                    unsigned bits = rj[t];
                     while (bits) {
-                        const int i = wd * 32 + __ffs(bits) - 1;
+                        const int i = t * 32 + __ffs(bits) - 1;
                         bits &= bits - 1;
                         const unsigned *ri = R + i * W;
                         int k = 0;
-                        for (int t = (i >> 5); t < W; ++t) {
-                            unsigned x = rj[t] & ri[t];
-                            k += __popc(x);
-                            while (x) { atomicAdd(&kc[t * 32 + __ffs(x) - 1], 1); x &= x - 1; }
+                        for (int tt = i >> 5; tt < W; ++tt) k += __popc(rj[tt] & ri[tt]);
+                        if (k) {
+                            kj += k;
+                            atomicAdd(&kc[i], k);
                         }
-                        if (!k) continue;
-                        ku += k;
-                        atomicAdd(&kc[j], k);
-                        atomicAdd(&kc[i], k);
                     }
                 }
+                kj = warp_sum(kj);
+                if (lane == 0 && kj) {
+                    atomicAdd(&kc[j], (int)kj);
+                    ku += kj;
+                }
+            }
+            // Columns: C[x] = rows j with x in R[j], built with ballots; each
+            // j in C[x] closes popc(R[j] & C[x]) K4s with x as the fourth.
+            unsigned *col = colbuf + wid * 32;
+            for (;;) {
+                int x = 0;
+                if (lane == 0) x = atomicAdd(&work[1], 1);
+                x = __shfl_sync(FULL, x, 0);
+                if (x >= dp) break;
+                for (int t = 0; t < W; ++t) {
+                    const int j = t * 32 + lane;
+                    const bool bit = j < dp && ((R[j * W + (x >> 5)] >> (x & 31)) & 1u);
+                    const unsigned c = __ballot_sync(FULL, bit);
+                    if (lane == 0) col[t] = c;
+                }
+                __syncwarp();
+                long long kx = 0;
+                for (int t = lane; t < W; t += 32) {
+                    unsigned bits = col[t];
+                    while (bits) {
+                        const int j = t * 32 + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const unsigned *rj = R + j * W;
+                        int k = 0;
+                        for (int tt = j >> 5; tt < W; ++tt) k += __popc(rj[tt] & col[tt]);
+                        kx += k;
+                    }
+                }
+                kx = warp_sum(kx);
+                if (lane == 0 && kx) atomicAdd(&kc[x], (int)kx);
+                __syncwarp();
             }
         }
         __syncthreads();

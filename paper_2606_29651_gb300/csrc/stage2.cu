@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
         const int umax = g.ncol[e - 1];
         __syncthreads();
         long long du12 = 0;
-        for (int jb = wid * 32; jb < dp - 1; jb += NW * 32) {
+        for (int jb = 0; jb < dp - 1; jb += 32) {   // all warps share each chunk
             const int j = jb + lane;
             int len = 0, vs = 0;
             if (j < dp - 1 && tcnt[s + j] > 0) {
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
             }
             int mypre;
             const int total = seg_build(seg, vs, len, mypre);
-            seg_visit<4>(g.ncol, seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            seg_visit<4>(g.ncol, seg, mypre, len, total, wid * 32, NW * 32, [&](bool valid, int q, int pos, int w) {
                 int i = -1;
                 if (valid && w <= umax) {
                     if (use_hash) {
