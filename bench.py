@@ -55,10 +55,9 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     B_c4  = 4 * number of wedges u - v - w with v, w below u (cycle roots)
     B_csr = 4 (n + 1) + 4 m, B_out = 120 n.
     A root's wedges (or triangle probes) count for the tier kernel that
-    takes it: 4-cycle roots by the bound sum over in-neighbours of (d_v - 1)
-    (warp <= 1536 with a packed table, packed mid <= 6144, split mid <= 3072,
-    cta <= 12288, else global), triangle roots by out-degree (warp <= 64,
-    else cta).
+    takes it: 4-cycle roots by their wedge count W (warp <= 1536 with a
+    packed table, packed mid <= 6144, split mid <= 3072, cta <= 12288, else
+    global), triangle roots by out-degree (warp <= 64, else cta).
     """
     n = len(rowptr) - 1
     m = len(colidx)
@@ -66,8 +65,6 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     order = np.lexsort((np.arange(n), deg_class(d)))
     rank = np.empty(n, np.int64)
     rank[order] = np.arange(n)
-    dr = np.empty(n, np.int64)
-    dr[rank] = d                                   # degree by new id
     src = np.repeat(np.arange(n), d)
     rs, rd = rank[src], rank[colidx.astype(np.int64)]
     out = rd > rs
@@ -84,16 +81,15 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     pos = np.arange(m) - start[rs2]
     sel = rd2 > rs2                                # entry (v -> u), u > v: pos wedges below u
     w_root = np.bincount(rd2[sel], weights=pos[sel], minlength=n)
-    ub_root = np.bincount(rd2[sel], weights=dr[rs2[sel]] - 1, minlength=n)
     din = np.bincount(rd2[sel], minlength=n)
-    live = (din >= 2) & (ub_root >= 2)
+    live = (din >= 2) & (w_root >= 2)
     pack_lim = (1 << (32 - int(n - 1).bit_length())) - 2     # packed tables hold counts below this
-    warp = live & (ub_root <= min(c4_warp_ub, pack_lim))
-    midp = live & ~warp & (ub_root <= 6144) & (ub_root <= pack_lim)
-    mid = live & ~warp & ~midp & (ub_root <= 3072)
-    cta = live & ~warp & ~midp & ~mid & (ub_root <= 12288)
+    warp = live & (w_root <= min(c4_warp_ub, pack_lim))
+    midp = live & ~warp & (w_root <= 6144) & (w_root <= pack_lim)
+    mid = live & ~warp & ~midp & (w_root <= 3072)
+    cta = live & ~warp & ~midp & ~mid & (w_root <= 12288)
     tiers = {"k_c4_warp": warp, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
-             "k_c4_global": live & (ub_root > 12288)}
+             "k_c4_global": live & (w_root > 12288)}
     w_c4 = int(w_root.sum())
     res = {"B_csr": 4 * (n + 1) + 4 * m, "B_tri": b_tri, "B_c4": 4 * w_c4, "W_c4": w_c4, "B_out": 120 * n,
            "tri_probes": b_tri // 4}

@@ -10,11 +10,12 @@
 // then
 //   u gets sum_w C(c_w, 2), w gets C(c_w, 2),
 //   each middle vertex v gets sum over its wedges of (c_w - 1).
-// The wedges through v are the entries of row v below u; the whole row is
-// streamed (it is read anyway) and filtered, so there is no dependent search.
-// Roots are routed by the bound UB = sum over v of (d_v - 1) >= wedges
-// (a count is at most UB too): one warp, four warps, a 512-thread CTA, or a
-// CTA with a dense count row in global memory. Tables are open-addressing
+// The wedges through v are the entries of row v below u: a prefix of row v
+// whose length the triangle stage left at the in-entry (u, v) of `tcnt`
+// (clamped to the row, so that no input can send a read outside it). Roots
+// are routed by their wedge count W (a count is at most W too): one warp,
+// four warps, a 512-thread CTA, or a CTA with a dense count row in global
+// memory. Tables are open-addressing
 // hash tables in shared memory, either split (key and count arrays) or
 // packed (key << cb | count in one 32-bit word, cb = 32 - bits(n - 1) count
 // bits, usable while UB < 2^cb - 1), which holds twice the keys in the same
@@ -38,11 +39,19 @@ constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
+// Wedge-segment length through the in-entry at position p of a root's row
+// (left there by the triangle stage), clamped to the row of v.
+__device__ __forceinline__ int wedge_len(const int *wlen, int p, const int4 &rv) {
+    const int l = wlen[p];
+    return l < 0 ? 0 : (l > rv.z - rv.x ? rv.z - rv.x : l);
+}
+
 // Segment table of in-neighbour chunk cb of root u in the calling warp: the
-// rows of v = ncol[b + cb + lane] concatenated. Returns the total length; the
-// lane's own v, segment length and offset come back in v, len, pre.
-__device__ __forceinline__ int wedge_chunk(const Graph &g, int b, int din, int cb, SegTab &T, int &v, int &len,
-                                           int &pre) {
+// wedge prefixes of the rows of v = ncol[b + cb + lane] concatenated. Returns
+// the total length; the lane's own v, segment length and offset come back in
+// v, len, pre.
+__device__ __forceinline__ int wedge_chunk(const Graph &g, const int *wlen, int b, int din, int cb, SegTab &T, int &v,
+                                           int &len, int &pre) {
     const int p = cb + lane_id();
     int st = 0;
     v = -1;
@@ -51,22 +60,22 @@ __device__ __forceinline__ int wedge_chunk(const Graph &g, int b, int din, int c
         v = g.ncol[b + p];
         const int4 rv = g.rinfo[v];
         st = rv.x;
-        len = rv.z - rv.x;
+        len = wedge_len(wlen, b + p, rv);
     }
     return seg_build(T, st, len, pre);
 }
 
 // Walks the wedges of root u (in-neighbours b .. b + din of row u), one warp
 // per chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...): f(act, q, w) on
-// every lane, act meaning that w is an entry below u of the row of the v
-// owned by lane q; then done(v) per chunk.
+// every lane, act meaning that w is a wedge end through the v owned by lane
+// q; then done(v) per chunk.
 template <class F, class D>
-__device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep, SegTab &T, F f,
-                                            D done) {
+__device__ __forceinline__ void walk_wedges(const Graph &g, const int *wlen, int b, int din, int c0, int cstep,
+                                            SegTab &T, F f, D done) {
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
         int v, len, pre;
-        const int total = wedge_chunk(g, b, din, cb, T, v, len, pre);
-        seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok && w < u, q, w); });
+        const int total = wedge_chunk(g, wlen, b, din, cb, T, v, len, pre);
+        seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
         __syncwarp();
         done(v);
         __syncwarp();
@@ -77,13 +86,12 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
 // table of each chunk and takes the windows wid, wid + nw, ... of 32
 // elements. With DONE, warp 0 calls done(v) after the CTA finished the chunk.
 template <bool DONE, class F, class D>
-__device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, int din, int wid, int nw, SegTab &T,
-                                                F f, D done) {
+__device__ __forceinline__ void walk_wedges_cta(const Graph &g, const int *wlen, int b, int din, int wid, int nw,
+                                                SegTab &T, F f, D done) {
     for (int cb = 0; cb < din; cb += 32) {
         int v, len, pre;
-        const int total = wedge_chunk(g, b, din, cb, T, v, len, pre);
-        seg_visit<4>(g.ncol, T, pre, len, total, wid * 32, nw * 32,
-                     [&](bool ok, int q, int, int w) { f(ok && w < u, q, w); });
+        const int total = wedge_chunk(g, wlen, b, din, cb, T, v, len, pre);
+        seg_visit<4>(g.ncol, T, pre, len, total, wid * 32, nw * 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
         if (DONE) {
             __syncthreads();
             if (wid == 0) done(v);
@@ -166,8 +174,9 @@ struct PackedTab {
 // pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
 // the CTA).
 template <bool CTA, class Tab>
-__device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din, const Tab &T, int wid,
-                                        int nw, int tid, int nthreads, SegTab &seg, long long *pv, int *any_cycle) {
+__device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *vacc, int u, int b, int din,
+                                        const Tab &T, int wid, int nw, int tid, int nthreads, SegTab &seg,
+                                        long long *pv, int *any_cycle) {
     const int lane = lane_id();
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
@@ -182,8 +191,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         base = __shfl_sync(FULL, base, __ffs(fresh) - 1);
         if (slot >= 0) T.touched[base + __popc(fresh & lanemask_lt())] = (unsigned short)slot;
     };
-    if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
-    else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {});
+    if (CTA) walk_wedges_cta<false>(g, wlen, b, din, wid, nw, seg, insert, [](int) {});
+    else walk_wedges(g, wlen, b, din, 0, 1, seg, insert, [](int) {});
     sync();
     const int nt = *T.ntouched;
     long long su = 0;
@@ -214,8 +223,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
             if (x) add64(&vacc[v].C4, x);
             pv[lane] = 0;
         };
-        if (CTA) walk_wedges_cta<true>(g, u, b, din, wid, nw, seg, middle, flush);
-        else walk_wedges(g, u, b, din, 0, 1, seg, middle, flush);
+        if (CTA) walk_wedges_cta<true>(g, wlen, b, din, wid, nw, seg, middle, flush);
+        else walk_wedges(g, wlen, b, din, 0, 1, seg, middle, flush);
     }
     sync();
     for (int i = tid; i < nt; i += nthreads) T.clear(T.touched[i]);
@@ -238,8 +247,8 @@ struct C4WarpSmem {
 
 // One warp per root with UB <= maxub (<= CW_MAXUB) that fits a packed table;
 // other roots are queued for the wider tiers.
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters,
-                                                           int maxub, int cb) {
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *wlen, VAcc *vacc, int *lists,
+                                                           int *counters, int maxub, int cb) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -254,11 +263,8 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
         if (din < 2) continue;
-        long long ub = 0;
-        for (int p = lane; p < din; p += 32) {
-            const int4 rv = g.rinfo[g.ncol[b + p]];
-            ub += rv.z - rv.x - 1;
-        }
+        long long ub = 0;   // exact wedge count W of root u
+        for (int p = lane; p < din; p += 32) ub += wedge_len(wlen, b + p, g.rinfo[g.ncol[b + p]]);
         ub = warp_sum(ub);
         if (ub < 2) continue;
         if (ub > maxub || ub > pack_lim) {
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             }
             continue;
         }
-        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, &S.any_cycle);
+        c4_root<false>(g, wlen, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, &S.any_cycle);
     }
 }
 
@@ -280,7 +286,8 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
 // 2 x SLOTS packed ones) lives in dynamic shared memory and is emptied once
 // per CTA.
 template <int THREADS, int SLOTS, int MAXUB, bool PACKED>
-__device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count, int cb) {
+__device__ __forceinline__ void c4_queue(const Graph &g, const int *wlen, VAcc *vacc, const int *list, int count,
+                                         int cb) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
     constexpr int NT = PACKED ? 2 * MAXUB : MAXUB;   // touched capacity
@@ -303,11 +310,11 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
         const int4 ru = g.rinfo[u];
         if (PACKED) {
             const PackedTab T{words, 2 * SLOTS - 1, cb, touched, &flags[0]};
-            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
+            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
         } else {
             const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS - 1,
                              touched, &flags[0]};
-            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
+            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
         }
     }
 }
@@ -319,19 +326,19 @@ constexpr size_t cq_smem(int threads, int slots, int maxub) {
 constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXUB);
 constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXUB);
 
-__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists, const int *counters,
-                                                       int cb) {
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
+__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, const int *wlen, VAcc *vacc, const int *lists,
+                                                       const int *counters, int cb) {
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, false>(g, wlen, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
 }
 
-__global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, VAcc *vacc, const int *lists, const int *counters,
-                                                        int cb) {
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
+__global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, const int *wlen, VAcc *vacc, const int *lists,
+                                                        const int *counters, int cb) {
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, true>(g, wlen, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
 }
 
-__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists, const int *counters,
-                                                       int cb) {
-    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
+__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, const int *wlen, VAcc *vacc, const int *lists,
+                                                       const int *counters, int cb) {
+    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, wlen, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
 }
 
 // Zero the dense rows of the global tier (only when that tier has work).
@@ -353,8 +360,8 @@ __global__ void k_c4_zero_dense(int *dense, long long n, int slots, const int *c
 // Pass 1 adds every wedge; pass 2 reads each count (per middle vertex) and
 // marks the key with the sign bit, so that exactly one visitor credits
 // C(c, 2) to w; pass 3 stores zeros back.
-__global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, const int *lists, const int *counters,
-                                                          int *dense, int slots) {
+__global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, const int *wlen, VAcc *vacc, const int *lists,
+                                                          const int *counters, int *dense, int slots) {
     constexpr int NW = CG_THREADS / 32;
     __shared__ SegTab segs[NW];
     __shared__ long long pvs[NW][32];
@@ -370,11 +377,11 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
         pv[lane] = 0;
-        walk_wedges(g, u, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); },
+        walk_wedges(g, wlen, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); },
                     [&](int) {});
         __syncthreads();
         long long su = 0;
-        walk_wedges(g, u, b, din, wid, NW, seg,
+        walk_wedges(g, wlen, b, din, wid, NW, seg,
                     [&](bool act, int q, int w) {
                         if (!act) return;
                         const int old = atomicOr(&row[w], (int)0x80000000);
@@ -393,7 +400,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, VAcc *vacc, c
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
         __syncthreads();
-        walk_wedges(g, u, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) row[w] = 0; }, [&](int) {});
+        walk_wedges(g, wlen, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) row[w] = 0; }, [&](int) {});
         __syncthreads();
     }
 }
@@ -410,18 +417,20 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxub = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXUB ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXUB;
     const int cb = packed_count_bits(w.n);
-    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxub, cb);
+    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, maxub,
+                                                                         cb);
     after_launch(st, K_C4_WARP);
-    k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MIDP);
-    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MID);
-    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
     if (w.c4slots > 0) {
         k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, w.n, w.c4slots, w.counters);
         after_launch(st, K_C4_ZERO);
-        k_c4_global<<<w.c4slots, CG_THREADS, 0, st>>>(g, w.vacc, w.lists, w.counters, w.c4dense, w.c4slots);
+        k_c4_global<<<w.c4slots, CG_THREADS, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, w.c4dense,
+                                                      w.c4slots);
         after_launch(st, K_C4_GLOBAL);
     }
 }

@@ -45,6 +45,15 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
+        // Wedge lengths for the 4-cycle stage: for every out-neighbour x of u,
+        // the entries of row u below x number (s - ru.x) + j; they are stored
+        // at the in-entry of u in row x (a slot of tcnt t does not use).
+        for (int j = lane; j < dp; j += 32) {
+            const int x = g.ncol[s + j];
+            const int4 rx = g.rinfo[x];
+            const int q = lower_bound(g.ncol, rx.x, rx.y, u);
+            if (q < rx.y && g.ncol[q] == u) tcnt[q] = (s - ru.x) + j;
+        }
         if (dp < 2) continue;
         if (dp > maxd) {
             if (lane == 0) heavy[atomicAdd(&counters[CNT_TRI_HEAVY], 1)] = u;
@@ -315,6 +324,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
 void launch_stage1(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxd = w.tune[TUNE_WARP_MAXD] < TW_MAXD ? w.tune[TUNE_WARP_MAXD] : TW_MAXD;
+    // (k_tri_warp also leaves, in the in-entries of tcnt, the wedge lengths
+    // that the 4-cycle stage reads)
     k_tri_warp<<<w.num_sms * w.tune[TUNE_GRID_TRI], TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
                                                                           maxd);
     after_launch(st, K_TRI_WARP);
