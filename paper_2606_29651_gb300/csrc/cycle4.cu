@@ -106,49 +106,43 @@ __device__ __forceinline__ void walk_wedges_cta(const Graph &g, const int *wlen,
 struct SplitTab {
     int *hk, *hc;
     unsigned mask;
-    unsigned short *touched;
-    int *ntouched;
-    // counts w; returns the slot if this call inserted w, else -1
+    unsigned short *touched;   // slots filled (CTA groups)
+    // counts w; returns the slot if this call inserted w, -1 if w was there
     __device__ __forceinline__ int add(int w) const {
         unsigned s = hash_slot(w, mask);
         for (unsigned probe = 0; probe <= mask; ++probe) {
-            int k = hk[s];
-            if (k == -1) {
-                const int prev = atomicCAS(&hk[s], -1, w);
-                if (prev == -1) { atomicAdd(&hc[s], 1); return (int)s; }
-                k = prev;
-            }
-            if (k == w) { atomicAdd(&hc[s], 1); return -1; }
+            const int prev = atomicCAS(&hk[s], -1, w);
+            if (prev == -1) { atomicAdd(&hc[s], 1); return (int)s; }
+            if (prev == w) { atomicAdd(&hc[s], 1); return -1; }
             s = (s + 1) & mask;
         }
         return -1;
     }
     __device__ __forceinline__ int get(int w) const { return hcount_get(hk, hc, mask, w); }
+    __device__ __forceinline__ bool empty(int s) const { return hk[s] == -1; }
     __device__ __forceinline__ int key(int s) const { return hk[s]; }
     __device__ __forceinline__ int cnt(int s) const { return hc[s]; }
     __device__ __forceinline__ void clear(int s) const { hk[s] = -1; hc[s] = 0; }
+    __device__ __forceinline__ void clear_all(int tid, int nthreads) const {
+        for (int i = tid; i <= (int)mask; i += nthreads) { hk[i] = -1; hc[i] = 0; }
+    }
 };
 
 // Packed table: one word (w << cb) | count per slot, EMPTY when free. A
-// count never reaches 2^cb - 1 (the caller ensures UB < 2^cb - 1), so a full
+// count never reaches 2^cb - 1 (the caller ensures W < 2^cb - 1), so a full
 // word is never EMPTY.
 struct PackedTab {
     unsigned *t;
     unsigned mask;
     int cb;
-    unsigned short *touched;
-    int *ntouched;
+    unsigned short *touched;   // slots filled (CTA groups)
     __device__ __forceinline__ int add(int w) const {
         const unsigned key = static_cast<unsigned>(w);
         unsigned s = hash_slot(w, mask);
         for (unsigned probe = 0; probe <= mask; ++probe) {
-            unsigned cur = t[s];
-            if (cur == EMPTY) {
-                const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
-                if (prev == EMPTY) return (int)s;
-                cur = prev;
-            }
-            if ((cur >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
+            const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
+            if (prev == EMPTY) return (int)s;
+            if ((prev >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
             s = (s + 1) & mask;
         }
         return -1;
@@ -164,53 +158,70 @@ struct PackedTab {
         }
         return 0;
     }
+    __device__ __forceinline__ bool empty(int s) const { return t[s] == EMPTY; }
     __device__ __forceinline__ int key(int s) const { return (int)(t[s] >> cb); }
     __device__ __forceinline__ int cnt(int s) const { return (int)(t[s] & ((1u << cb) - 1)); }
     __device__ __forceinline__ void clear(int s) const { t[s] = EMPTY; }
+    __device__ __forceinline__ void clear_all(int tid, int nthreads) const {
+        uint4 *t4 = reinterpret_cast<uint4 *>(t);
+        for (int i = tid; i < (int)(mask + 1) / 4; i += nthreads) t4[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+    }
 };
 
 // Counts all wedges of u into the table and credits every 4-cycle rooted at
 // u. Every thread of the group (one warp, or a CTA with CTA = true) calls it.
+// A repeated key is a 4-cycle, so roots without one skip the credit and
+// middle passes. A CTA records the slots it fills in `touched` (flags[0]
+// counts them, flags[1] notes a repeated key) and empties only those; a warp
+// keeps no list: its table is sized to the root (at least twice W slots),
+// and it sweeps that region.
 // pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
 // the CTA).
 template <bool CTA, class Tab>
 __device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *vacc, int u, int b, int din,
                                         const Tab &T, int wid, int nw, int tid, int nthreads, SegTab &seg,
-                                        long long *pv, int *any_cycle) {
+                                        long long *pv, int *flags) {
     const int lane = lane_id();
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
     };
+    bool dup_l = false;   // warp group: this lane saw a repeated key
     auto insert = [&](bool act, int, int w) {
-        const int slot = act ? T.add(w) : -1;
-        // new keys of the warp take consecutive `touched` entries: one atomic
+        const int slot = act ? T.add(w) : -2;
+        if (!CTA) {
+            dup_l |= slot == -1;
+            return;
+        }
+        // new keys of the warp take consecutive `touched` entries
         const unsigned fresh = __ballot_sync(FULL, slot >= 0);
-        if (!fresh) return;
+        const unsigned dups = __ballot_sync(FULL, slot == -1);
+        if (!(fresh | dups)) return;
         int base = 0;
-        if (lane == __ffs(fresh) - 1) base = atomicAdd(T.ntouched, __popc(fresh));
-        base = __shfl_sync(FULL, base, __ffs(fresh) - 1);
-        if (slot >= 0) T.touched[base + __popc(fresh & lanemask_lt())] = (unsigned short)slot;
+        if (fresh && lane == __ffs(fresh) - 1) base = atomicAdd(&flags[0], __popc(fresh));
+        if (dups && lane == 0) flags[1] = 1;
+        if (slot >= 0) {
+            base = __shfl_sync(fresh, base, __ffs(fresh) - 1);
+            T.touched[base + __popc(fresh & lanemask_lt())] = (unsigned short)slot;
+        }
     };
     if (CTA) walk_wedges_cta<false>(g, wlen, b, din, wid, nw, seg, insert, [](int) {});
     else walk_wedges(g, wlen, b, din, 0, 1, seg, insert, [](int) {});
     sync();
-    const int nt = *T.ntouched;
-    long long su = 0;
-    for (int i = tid; i < nt; i += nthreads) {
-        const int slot = T.touched[i];
-        const int c = T.cnt(slot);
-        if (c >= 2) {
-            su += c2(c);
-            add64(&vacc[T.key(slot)].C4, c2(c));
+    const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
+    if (CTA ? flags[1] != 0 : __any_sync(FULL, dup_l)) {
+        long long su = 0;
+        for (int i = tid; i < nt; i += nthreads) {
+            const int slot = CTA ? T.touched[i] : i;
+            if (!CTA && T.empty(slot)) continue;
+            const int c = T.cnt(slot);
+            if (c >= 2) {
+                su += c2(c);
+                add64(&vacc[T.key(slot)].C4, c2(c));
+            }
         }
-    }
-    su = warp_sum(su);
-    if (lane == 0 && su) {
-        add64(&vacc[u].C4, su);
-        *any_cycle = 1;
-    }
-    sync();
-    if (*any_cycle) {   // middle vertices, only when some cycle is rooted at u
+        su = warp_sum(su);
+        if (lane == 0 && su) add64(&vacc[u].C4, su);
+        // middle vertices: each wedge through v adds c_w - 1
         if (tid < 32) pv[tid] = 0;
         sync();
         auto middle = [&](bool act, int q, int w) {
@@ -225,27 +236,30 @@ __device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *v
         };
         if (CTA) walk_wedges_cta<true>(g, wlen, b, din, wid, nw, seg, middle, flush);
         else walk_wedges(g, wlen, b, din, 0, 1, seg, middle, flush);
+        sync();
     }
-    sync();
-    for (int i = tid; i < nt; i += nthreads) T.clear(T.touched[i]);
-    sync();
-    if (tid == 0) {
-        *T.ntouched = 0;
-        *any_cycle = 0;
+    if (CTA) {
+        for (int i = tid; i < nt; i += nthreads) T.clear(T.touched[i]);
+        sync();
+        if (tid == 0) {
+            flags[0] = 0;
+            flags[1] = 0;
+        }
+    } else {
+        T.clear_all(tid, nthreads);
     }
     sync();
 }
 
-struct C4WarpSmem {
+constexpr int CW_MIN_SLOTS = 64;
+
+struct __align__(16) C4WarpSmem {
     unsigned t[CW_SLOTS];
-    unsigned short touched[CW_MAXUB];
     SegTab seg;
     long long pv[32];
-    int ntouched;
-    int any_cycle;
 };
 
-// One warp per root with UB <= maxub (<= CW_MAXUB) that fits a packed table;
+// One warp per root with W <= maxub (<= CW_MAXUB) that fits a packed table;
 // other roots are queued for the wider tiers.
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *wlen, VAcc *vacc, int *lists,
                                                            int *counters, int maxub, int cb) {
@@ -254,11 +268,9 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *w
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const long long pack_lim = (1ll << cb) - 2;   // largest UB a packed count may reach
-    for (int i = lane; i < CW_SLOTS; i += 32) S.t[i] = EMPTY;
-    if (lane == 0) { S.ntouched = 0; S.any_cycle = 0; }
+    const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
+    PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
     __syncwarp();
-    const PackedTab T{S.t, CW_SLOTS - 1, cb, S.touched, &S.ntouched};
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
@@ -278,7 +290,11 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *w
             }
             continue;
         }
-        c4_root<false>(g, wlen, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, &S.any_cycle);
+        // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
+        unsigned slots = next_pow2(2 * (unsigned)ub);
+        slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
+        const PackedTab T{S.t, slots - 1, cb, nullptr};
+        c4_root<false>(g, wlen, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr);
     }
 }
 
@@ -290,12 +306,12 @@ __device__ __forceinline__ void c4_queue(const Graph &g, const int *wlen, VAcc *
                                          int cb) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
-    constexpr int NT = PACKED ? 2 * MAXUB : MAXUB;   // touched capacity
+    constexpr int NT = PACKED ? 2 * MAXUB : MAXUB;   // touched capacity: every key of a root
     unsigned *words = reinterpret_cast<unsigned *>(dsm);            // 2 x SLOTS words
     unsigned short *touched = reinterpret_cast<unsigned short *>(words + 2 * SLOTS);
     SegTab *segs = reinterpret_cast<SegTab *>(touched + NT);         // one per warp
     long long *pv = reinterpret_cast<long long *>(segs + NW);        // 32, shared by the CTA
-    int *flags = reinterpret_cast<int *>(pv + 32);                  // ntouched, any_cycle
+    int *flags = reinterpret_cast<int *>(pv + 32);                  // new keys, repeated key
     const int wid = threadIdx.x >> 5;
     SegTab &seg = segs[wid];
     if (PACKED) {
@@ -309,12 +325,12 @@ __device__ __forceinline__ void c4_queue(const Graph &g, const int *wlen, VAcc *
         const int u = list[h];
         const int4 ru = g.rinfo[u];
         if (PACKED) {
-            const PackedTab T{words, 2 * SLOTS - 1, cb, touched, &flags[0]};
-            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
+            const PackedTab T{words, 2 * SLOTS - 1, cb, touched};
+            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
         } else {
             const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS - 1,
-                             touched, &flags[0]};
-            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, &flags[1]);
+                             touched};
+            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
         }
     }
 }
