@@ -57,7 +57,8 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     A root's wedges (or triangle probes) count for the tier kernel that
     takes it: 4-cycle roots by their wedge count W (warp <= 1536 with a
     packed table, packed mid <= 6144, split mid <= 3072, cta <= 12288, else
-    global), triangle roots by out-degree (warp <= 64, else cta).
+    global), triangle roots by out-degree (warp <= 64, cta <= 256, else
+    big).
     """
     n = len(rowptr) - 1
     m = len(colidx)
@@ -72,7 +73,9 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     probes = np.minimum(dplus[rs[out]], dplus[rd[out]])
     tri_root = rs[out]
     b_tri = 4 * int(probes.sum())
-    b_tri_cta = 4 * int(probes[dplus[tri_root] > warp_maxd].sum())
+    droot = dplus[tri_root]
+    b_tri_cta = 4 * int(probes[(droot > warp_maxd) & (droot <= 256)].sum())
+    b_tri_big = 4 * int(probes[droot > 256].sum())
     # wedges rooted at u through in-neighbour v: entries of row v below u
     o2 = np.lexsort((rd, rs))
     rs2, rd2 = rs[o2], rd[o2]
@@ -93,7 +96,7 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     w_c4 = int(w_root.sum())
     res = {"B_csr": 4 * (n + 1) + 4 * m, "B_tri": b_tri, "B_c4": 4 * w_c4, "W_c4": w_c4, "B_out": 120 * n,
            "tri_probes": b_tri // 4}
-    per_kernel = {"k_tri_warp": b_tri - b_tri_cta, "k_tri_cta": b_tri_cta,
+    per_kernel = {"k_tri_warp": b_tri - b_tri_cta - b_tri_big, "k_tri_cta": b_tri_cta, "k_tri_big": b_tri_big,
                   "k_relabel_rows_warp": 2 * res["B_csr"], "k_solve": res["B_csr"] + res["B_out"]}
     for k, msk in tiers.items():
         per_kernel[k] = 4 * int(w_root[msk].sum())

@@ -46,8 +46,10 @@ enum TuneIndex {
 };
 
 // Indices into Work::counters.
+// The triangle and aggregate heavy lists hold two tiers each: CTA-sized
+// roots from the front (CNT_*_HEAVY), the largest from the back (CNT_*_BIG).
 enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_GLOBAL = 3, CNT_DMAX = 4, CNT_C4_MID = 5,
-       CNT_C4_MIDP = 6 };
+       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8 };
 
 constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
 constexpr int SCAN_TILE = 4096;      // elements per scan block
@@ -70,7 +72,7 @@ void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *st
 enum KernelId {
     K_CLASS_HIST, K_SCAN, K_CLASS_SCATTER, K_RELABEL_WARP, K_RELABEL_CTA, K_BATCH_SETUP,
     K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_ZERO, K_C4_GLOBAL,
-    K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_COUNT
+    K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_COUNT
 };
 const char *kernel_name(int id);
 

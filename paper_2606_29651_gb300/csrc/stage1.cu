@@ -24,6 +24,7 @@ namespace niorca {
 // ----------------------------------------------------------- warp tier
 
 constexpr int TW_MAXD = 64;   // out-degree handled by one warp
+constexpr int TS_MAXD = 256;  // out-degree handled by a 256-thread CTA (k_tri_cta)
 constexpr int TW_WARPS = 8;
 
 struct TriWarpSmem {
@@ -55,7 +56,10 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
         const int s = ru.y, e = ru.z, dp = e - s;
         if (dp < 2 || dp > maxd) {
             for (int j = lane; j < dp; j += 32) wedge_length(u, ru, j, g.rinfo[g.ncol[s + j]]);
-            if (dp > maxd && lane == 0) heavy[atomicAdd(&counters[CNT_TRI_HEAVY], 1)] = u;
+            if (dp > maxd && lane == 0) {
+                if (dp <= TS_MAXD) heavy[atomicAdd(&counters[CNT_TRI_HEAVY], 1)] = u;
+                else heavy[g.n - 1 - atomicAdd(&counters[CNT_TRI_BIG], 1)] = u;
+            }
             continue;
         }
         const unsigned mask = next_pow2(2 * dp) - 1;
@@ -133,21 +137,34 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
     }
 }
 
-// ------------------------------------------------------------ CTA tier
+// ------------------------------------------------------------ CTA tiers
 
-constexpr int TC_THREADS = 256;
-constexpr int TC_BITMAT_MAXD = 1024;   // roots up to this out-degree keep R in shared memory
-constexpr int TC_HASH_MAXD = 8192;     // beyond this, membership is a binary search in global
-constexpr size_t TC_SMEM = (size_t)2 * 2048 * 4          // hash keys + values (dp <= 1024)
-                           + (size_t)2 * TC_BITMAT_MAXD * 4  // cnt + kc
-                           + (size_t)TC_BITMAT_MAXD * (TC_BITMAT_MAXD / 32) * 4  // R
-                           + (size_t)(TC_THREADS / 32) * (sizeof(SegTab) + 128)  // segments, column words
-                           + 16;                                                 // work counters
-// Same budget re-cut for TC_BITMAT_MAXD < dp <= TC_HASH_MAXD: a 16384-slot
-// hash (128 KB) + cnt/kc (64 KB) + segments; checked on the host.
-constexpr size_t TC_SMEM_HASHONLY = (size_t)2 * 16384 * 4 + (size_t)2 * TC_HASH_MAXD * 4 +
-                                    (size_t)(TC_THREADS / 32) * (sizeof(SegTab) + 128) + 16;
-constexpr size_t TC_SMEM_MAX = TC_SMEM > TC_SMEM_HASHONLY ? TC_SMEM : TC_SMEM_HASHONLY;
+// Roots with out-degree above the warp tier get a CTA each, in two sizes:
+// k_tri_cta (256 threads, dp <= TS_MAXD) needs about 18 KB of shared memory,
+// so several CTAs share an SM; k_tri_big (1024 threads) takes the rest with
+// the bit matrix R up to TB_BITMAT_MAXD (hash of N+(u) capped at 2048 slots),
+// a 16384-slot hash up to TB_HASH_MAXD, and binary searches beyond.
+// k_tri_warp queues the first kind from the front of the heavy list and the
+// second from its back.
+constexpr int TS_THREADS = 256;
+constexpr int TB_THREADS = 1024;
+constexpr int TB_BITMAT_MAXD = 1152;
+constexpr int TB_BITMAT_HSLOTS = 2048;
+constexpr int TB_HASH_MAXD = 8192;
+
+// Dynamic shared memory of one CTA: hash keys + values (hslots), cnt + kc
+// (nloc), per warp a segment table and one column of R (colw words), 4 work
+// counters, and R (rows x ceil(rows / 32) words).
+constexpr size_t tc_smem(int threads, int hslots, int nloc, int colw, int rows) {
+    return (size_t)2 * hslots * 4 + (size_t)2 * nloc * 4 + (size_t)(threads / 32) * (sizeof(SegTab) + 4 * colw) +
+           16 + (size_t)rows * ((rows + 31) / 32) * 4;
+}
+constexpr size_t TS_SMEM = tc_smem(TS_THREADS, 2 * TS_MAXD, TS_MAXD, TS_MAXD / 32, TS_MAXD);
+constexpr size_t TB_SMEM_BITS =
+    tc_smem(TB_THREADS, TB_BITMAT_HSLOTS, TB_BITMAT_MAXD, (TB_BITMAT_MAXD + 31) / 32, TB_BITMAT_MAXD);
+constexpr size_t TB_SMEM_HASH = tc_smem(TB_THREADS, 2 * TB_HASH_MAXD, TB_HASH_MAXD, (TB_BITMAT_MAXD + 31) / 32, 0);
+constexpr size_t TB_SMEM = TB_SMEM_BITS > TB_SMEM_HASH ? TB_SMEM_BITS : TB_SMEM_HASH;
+static_assert(TB_SMEM <= 227 * 1024, "k_tri_big shared memory");
 
 __device__ __forceinline__ int out_index(const int *hk, const int *hv, unsigned mask, bool use_hash, const int *ncol,
                                          int s, int e, int w) {
@@ -156,31 +173,35 @@ __device__ __forceinline__ int out_index(const int *hk, const int *hv, unsigned 
     return p < 0 ? -1 : p - s;
 }
 
-__global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters) {
+// One CTA per root u of the list (roots list[0 .. count) or, with BACK,
+// list[n - 1], list[n - 2], ...).
+template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK>
+__device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, const int *list, int count) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    constexpr int NW = TC_THREADS / 32;
+    constexpr int TC_THREADS = THREADS;
+    constexpr int NW = THREADS / 32;
+    constexpr int COLW = (BITMAT_MAXD + 31) / 32;   // words of one column of R
     const int lane = lane_id(), wid = threadIdx.x >> 5;
-    const int nh = counters[CNT_TRI_HEAVY];
-    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int u = heavy[h];
+    for (int h = blockIdx.x; h < count; h += gridDim.x) {
+        const int u = BACK ? list[g.n - 1 - h] : list[h];
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
-        const bool use_bits = dp <= TC_BITMAT_MAXD;
-        const bool use_hash = dp <= TC_HASH_MAXD;
-        const unsigned H = use_hash ? next_pow2(2 * dp) : 0;
+        const bool use_bits = dp <= BITMAT_MAXD;
+        const bool use_hash = dp <= HASH_MAXD;
+        unsigned H = use_hash ? next_pow2(2 * dp) : 0;
+        if (use_bits && H > (unsigned)BITMAT_HSLOTS) H = BITMAT_HSLOTS;
         const unsigned mask = H ? H - 1 : 0;
         const int W = (dp + 31) >> 5;  // bit-matrix words per row
         // carve shared memory
-        // beyond TC_HASH_MAXD the per-position counters live in global memory
+        // beyond HASH_MAXD the per-position counters live in global memory
         const int nloc = use_hash ? dp : 0;
         int *hk = reinterpret_cast<int *>(dsm);
         int *hv = hk + H;
         int *cnt = hv + H;
         int *kc = cnt + nloc;
         SegTab *segs = reinterpret_cast<SegTab *>(kc + nloc);   // one per warp
-        unsigned *colbuf = reinterpret_cast<unsigned *>(segs + NW);  // NW x 32 column words
-        int *work = reinterpret_cast<int *>(colbuf + NW * 32);        // next row, next column
+        unsigned *colbuf = reinterpret_cast<unsigned *>(segs + NW);  // NW x COLW column words
+        int *work = reinterpret_cast<int *>(colbuf + NW * COLW);      // next row, next column
         unsigned *R = reinterpret_cast<unsigned *>(work + 4);
         SegTab &seg = segs[wid];
         for (int i = threadIdx.x; i < (int)H; i += TC_THREADS) hk[i] = -1;
@@ -283,7 +304,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
             }
             // Columns: C[x] = rows j with x in R[j], built with ballots; each
             // j in C[x] closes popc(R[j] & C[x]) K4s with x as the fourth.
-            unsigned *col = colbuf + wid * 32;
+            unsigned *col = colbuf + wid * COLW;
             for (;;) {
                 int x = 0;
                 if (lane == 0) x = atomicAdd(&work[1], 1);
@@ -322,6 +343,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
     }
 }
 
+__global__ void __launch_bounds__(TS_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
+                                                        const int *counters) {
+    tri_cta<TS_THREADS, TS_MAXD, 2 * TS_MAXD, TS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_TRI_HEAVY]);
+}
+
+__global__ void __launch_bounds__(TB_THREADS) k_tri_big(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
+                                                        const int *counters) {
+    tri_cta<TB_THREADS, TB_BITMAT_MAXD, TB_BITMAT_HSLOTS, TB_HASH_MAXD, true>(g, tcnt, vacc, heavy,
+                                                                            counters[CNT_TRI_BIG]);
+}
+
+
 void launch_stage1(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxd = w.tune[TUNE_WARP_MAXD] < TW_MAXD ? w.tune[TUNE_WARP_MAXD] : TW_MAXD;
@@ -330,12 +363,15 @@ void launch_stage1(Work &w, cudaStream_t st) {
     k_tri_warp<<<w.num_sms * w.tune[TUNE_GRID_TRI], TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
                                                                           maxd);
     after_launch(st, K_TRI_WARP);
-    k_tri_cta<<<w.num_sms * 1, TC_THREADS, TC_SMEM_MAX, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    k_tri_cta<<<w.num_sms * 6, TS_THREADS, TS_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
     after_launch(st, K_TRI_CTA);
+    k_tri_big<<<w.num_sms, TB_THREADS, TB_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    after_launch(st, K_TRI_BIG);
 }
 
 void configure_stage1() {
-    cudaFuncSetAttribute(k_tri_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM_MAX);
+    cudaFuncSetAttribute(k_tri_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TS_SMEM);
+    cudaFuncSetAttribute(k_tri_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TB_SMEM);
 }
 
 }  // namespace niorca

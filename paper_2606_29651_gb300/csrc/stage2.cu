@@ -18,6 +18,7 @@ namespace niorca {
 
 constexpr int AW_MAXD = 64;
 constexpr int AW_WARPS = 8;
+constexpr int AS_MAXD = 256;   // out-degree handled by a 256-thread CTA (k_agg_cta)
 
 struct AggWarpSmem {
     int hk[2 * AW_MAXD];
@@ -68,7 +69,10 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
         const int s = ru.y, e = ru.z, dp = e - s;
         if (dp < 1) continue;
         if (dp > maxd) {
-            if (lane == 0) heavy[atomicAdd(&counters[CNT_AGG_HEAVY], 1)] = u;
+            if (lane == 0) {
+                if (dp <= AS_MAXD) heavy[atomicAdd(&counters[CNT_AGG_HEAVY], 1)] = u;
+                else heavy[g.n - 1 - atomicAdd(&counters[CNT_AGG_BIG], 1)] = u;
+            }
             continue;
         }
         if (!edge_aggregates(g, tcnt, vacc, u, s, dp, lane, 32) || dp < 2) continue;
@@ -110,19 +114,30 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
     }
 }
 
-constexpr int AC_THREADS = 256;
-constexpr int AC_HASH_MAXD = 8192;
-constexpr size_t AC_SMEM = (size_t)2 * 16384 * 4 + (size_t)AC_HASH_MAXD * 8 + (size_t)(AC_THREADS / 32) * sizeof(SegTab);
+// Roots above the warp tier: k_agg_cta (256 threads, dp <= AS_MAXD, about
+// 10 KB of shared memory, several CTAs per SM) and k_agg_big (1024 threads;
+// a hash of N+(u) up to AB_HASH_MAXD, binary searches beyond), from the
+// front and the back of the heavy list.
+constexpr int AS_THREADS = 256;
+constexpr int AB_THREADS = 1024;
+constexpr int AB_HASH_MAXD = 8192;
+constexpr size_t ac_smem(int threads, int maxd) {
+    return (size_t)2 * (2 * maxd) * 4 + (size_t)maxd * 8 + (size_t)(threads / 32) * sizeof(SegTab);
+}
+constexpr size_t AS_SMEM = ac_smem(AS_THREADS, AS_MAXD);
+constexpr size_t AB_SMEM = ac_smem(AB_THREADS, AB_HASH_MAXD);
+static_assert(AB_SMEM <= 227 * 1024, "k_agg_big shared memory");
 
-__global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters) {
+template <int THREADS, int HASH_MAXD, bool BACK>
+__device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *vacc, const int *heavy, int nh) {
     extern __shared__ __align__(16) unsigned char dsm[];
+    constexpr int AC_THREADS = THREADS;
+    constexpr int AC_HASH_MAXD = HASH_MAXD;
     constexpr int NW = AC_THREADS / 32;
     __shared__ int any_tri;
     const int lane = lane_id(), wid = threadIdx.x >> 5;
-    const int nh = counters[CNT_AGG_HEAVY];
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int u = heavy[h];
+        const int u = BACK ? heavy[g.n - 1 - h] : heavy[h];
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
         if (threadIdx.x == 0) any_tri = 0;
@@ -190,6 +205,16 @@ __global__ void __launch_bounds__(AC_THREADS) k_agg_cta(Graph g, const int *tcnt
     }
 }
 
+__global__ void __launch_bounds__(AS_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
+                                                        const int *counters) {
+    agg_cta<AS_THREADS, AS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY]);
+}
+
+__global__ void __launch_bounds__(AB_THREADS) k_agg_big(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
+                                                        const int *counters) {
+    agg_cta<AB_THREADS, AB_HASH_MAXD, true>(g, tcnt, vacc, heavy, counters[CNT_AGG_BIG]);
+}
+
 void launch_stage2(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     int *heavy = w.lists + (size_t)w.n;
@@ -197,12 +222,15 @@ void launch_stage2(Work &w, cudaStream_t st) {
     k_agg_warp<<<w.num_sms * w.tune[TUNE_GRID_AGG], AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters,
                                                                           maxd);
     after_launch(st, K_AGG_WARP);
-    k_agg_cta<<<w.num_sms, AC_THREADS, AC_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    k_agg_cta<<<w.num_sms * 6, AS_THREADS, AS_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
     after_launch(st, K_AGG_CTA);
+    k_agg_big<<<w.num_sms, AB_THREADS, AB_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    after_launch(st, K_AGG_BIG);
 }
 
 void configure_stage2() {
-    cudaFuncSetAttribute(k_agg_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AC_SMEM);
+    cudaFuncSetAttribute(k_agg_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AS_SMEM);
+    cudaFuncSetAttribute(k_agg_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AB_SMEM);
 }
 
 }  // namespace niorca

@@ -61,10 +61,11 @@ def test_closed_forms(ni):
         assert_same(gpu_count(ni, *gg.complete_bipartite(a, b)), closed_complete_bipartite(a, b), f"K{a},{b}")
 
 
-def test_complete_graph_beyond_bitmatrix(ni):
-    # out-degrees above 1024 take the probing K4 path
-    n = 1040
-    assert_same(gpu_count(ni, *gg.complete(n)), np.tile(np.array(closed_complete(n)), (n, 1)), f"K{n}")
+def test_complete_graphs_across_triangle_tiers(ni):
+    # K1040: out-degrees up to 1039 use the 1152-row bit matrix of the
+    # 1024-thread tier; K1200: out-degrees above 1152 take its probing K4 path
+    for n in (1040, 1200):
+        assert_same(gpu_count(ni, *gg.complete(n)), np.tile(np.array(closed_complete(n)), (n, 1)), f"K{n}")
 
 
 def test_empty_and_edgeless(ni):
