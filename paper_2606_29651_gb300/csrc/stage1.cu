@@ -9,14 +9,16 @@
 // probes each element. A hit is a triangle (u, v, w):
 //   t(u,v) and t(u,w) are counted in shared memory and added once per root,
 //   t(v,w) is added to global memory at the position of w in row v.
-// The hits also fill R, the adjacency bit-matrix of N+(u) oriented upwards:
-// R[j] bit i <=> N+(u)[i] in N+(N+(u)[j]). A K4 u < v < w < x is then a
-// triangle (j, i) of R together with a common bit of R[j] and R[i], so the
-// K4 count of each triangle is popc(R[j] & R[i]) -- Algorithm 2's pairwise
-// test over `neigh` done as word-wide bit operations. In the CTA tier the
-// fourth vertex x is credited through its column C[x] = {j : x in R[j]}:
-// sum over j in C[x] of popc(R[j] & C[x]), so the cost follows the edges of
-// R and not the (much larger) number of K4s of dense hub neighbourhoods.
+// The hits also fill R, the adjacency bit-matrix of N+(u): in the warp tier
+// oriented upwards (R[j] bit i <=> N+(u)[i] in N+(N+(u)[j])), so that a K4
+// u < v < w < x is a triangle (j, i) of R together with a common bit of R[j]
+// and R[i] -- Algorithm 2's pairwise test over `neigh` done as word-wide bit
+// operations. In the CTA tiers R is kept symmetric: the K4s of u through
+// y = N+(u)[y] are the triangles of R at y, and twice their number is the sum
+// over the neighbours z of y in R of popc(R[y] & R[z]). A warp takes a row
+// and its lanes one neighbour z each, with the same word loop on every lane,
+// so the cost follows the edges of R and not the (much larger) number of K4s
+// of dense hub neighbourhoods.
 #include "kernels.h"
 
 namespace niorca {
@@ -153,16 +155,16 @@ constexpr int TB_BITMAT_HSLOTS = 2048;
 constexpr int TB_HASH_MAXD = 8192;
 
 // Dynamic shared memory of one CTA: hash keys + values (hslots), cnt + kc
-// (nloc), per warp a segment table and one column of R (colw words), 4 work
-// counters, and R (rows x ceil(rows / 32) words).
-constexpr size_t tc_smem(int threads, int hslots, int nloc, int colw, int rows) {
-    return (size_t)2 * hslots * 4 + (size_t)2 * nloc * 4 + (size_t)(threads / 32) * (sizeof(SegTab) + 4 * colw) +
-           16 + (size_t)rows * ((rows + 31) / 32) * 4;
+// (nloc), per warp a segment table and a 64-entry buffer of row indices,
+// 4 work words, and R (rows x an odd number of words, to spread the banks).
+constexpr int tc_rowstride(int rows) { return ((rows + 31) / 32) | 1; }
+constexpr size_t tc_smem(int threads, int hslots, int nloc, int rows) {
+    return (size_t)2 * hslots * 4 + (size_t)2 * nloc * 4 + (size_t)(threads / 32) * (sizeof(SegTab) + 128) + 16 +
+           (size_t)rows * tc_rowstride(rows) * 4;
 }
-constexpr size_t TS_SMEM = tc_smem(TS_THREADS, 2 * TS_MAXD, TS_MAXD, TS_MAXD / 32, TS_MAXD);
-constexpr size_t TB_SMEM_BITS =
-    tc_smem(TB_THREADS, TB_BITMAT_HSLOTS, TB_BITMAT_MAXD, (TB_BITMAT_MAXD + 31) / 32, TB_BITMAT_MAXD);
-constexpr size_t TB_SMEM_HASH = tc_smem(TB_THREADS, 2 * TB_HASH_MAXD, TB_HASH_MAXD, (TB_BITMAT_MAXD + 31) / 32, 0);
+constexpr size_t TS_SMEM = tc_smem(TS_THREADS, 2 * TS_MAXD, TS_MAXD, TS_MAXD);
+constexpr size_t TB_SMEM_BITS = tc_smem(TB_THREADS, TB_BITMAT_HSLOTS, TB_BITMAT_MAXD, TB_BITMAT_MAXD);
+constexpr size_t TB_SMEM_HASH = tc_smem(TB_THREADS, 2 * TB_HASH_MAXD, TB_HASH_MAXD, 0);
 constexpr size_t TB_SMEM = TB_SMEM_BITS > TB_SMEM_HASH ? TB_SMEM_BITS : TB_SMEM_HASH;
 static_assert(TB_SMEM <= 227 * 1024, "k_tri_big shared memory");
 
@@ -180,7 +182,6 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int TC_THREADS = THREADS;
     constexpr int NW = THREADS / 32;
-    constexpr int COLW = (BITMAT_MAXD + 31) / 32;   // words of one column of R
     const int lane = lane_id(), wid = threadIdx.x >> 5;
     for (int h = blockIdx.x; h < count; h += gridDim.x) {
         const int u = BACK ? list[g.n - 1 - h] : list[h];
@@ -192,6 +193,7 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
         if (use_bits && H > (unsigned)BITMAT_HSLOTS) H = BITMAT_HSLOTS;
         const unsigned mask = H ? H - 1 : 0;
         const int W = (dp + 31) >> 5;  // bit-matrix words per row
+        const int WP = W | 1;          // row stride of R
         // carve shared memory
         // beyond HASH_MAXD the per-position counters live in global memory
         const int nloc = use_hash ? dp : 0;
@@ -200,15 +202,16 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
         int *cnt = hv + H;
         int *kc = cnt + nloc;
         SegTab *segs = reinterpret_cast<SegTab *>(kc + nloc);   // one per warp
-        unsigned *colbuf = reinterpret_cast<unsigned *>(segs + NW);  // NW x COLW column words
-        int *work = reinterpret_cast<int *>(colbuf + NW * COLW);      // next row, next column
+        unsigned short *zb = reinterpret_cast<unsigned short *>(segs + NW) + wid * 64;  // 64 per warp
+        int *work = reinterpret_cast<int *>(reinterpret_cast<unsigned short *>(segs + NW) + NW * 64);
+        long long *ksum = reinterpret_cast<long long *>(work + 2);    // sum of kc over the rows
         unsigned *R = reinterpret_cast<unsigned *>(work + 4);
         SegTab &seg = segs[wid];
         for (int i = threadIdx.x; i < (int)H; i += TC_THREADS) hk[i] = -1;
         for (int i = threadIdx.x; i < nloc; i += TC_THREADS) { cnt[i] = 0; kc[i] = 0; }
         if (use_bits)
-            for (int i = threadIdx.x; i < dp * W; i += TC_THREADS) R[i] = 0;
-        if (threadIdx.x < 2) work[threadIdx.x] = 0;
+            for (int i = threadIdx.x; i < dp * WP; i += TC_THREADS) R[i] = 0;
+        if (threadIdx.x < 4) work[threadIdx.x] = 0;
         __syncthreads();
         if (use_hash)
             for (int i = threadIdx.x; i < dp; i += TC_THREADS) hset_insert(hk, hv, mask, g.ncol[s + i], i);
@@ -235,10 +238,11 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
                 const int jj = jb + q;
                 warp_add_int(hit, use_hash ? &cnt[jj] : &tcnt[s + jj], jj, 1);
                 if (use_bits) {
-                    const int word = jj * W + (i >> 5);
+                    const int word = jj * WP + (i >> 5);
                     const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
                     const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
                     if (hit && (peers & lanemask_lt()) == 0) atomicOr(&R[word], bits);
+                    if (hit) atomicOr(&R[i * WP + (jj >> 5)], 1u << (jj & 31));   // and its mirror
                 }
                 if (!hit) return;
                 atomicAdd(use_hash ? &cnt[i] : &tcnt[s + i], 1);
@@ -273,70 +277,51 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
         for (int i = threadIdx.x; i < nloc; i += TC_THREADS)
             if (cnt[i]) atomicAdd(&tcnt[s + i], cnt[i]);
         if (use_bits) {
-            // Rows: a warp takes row j, its lanes the set bits i of R[j];
-            // popc(R[j] & R[i]) K4s have v_j second and w_i third.
+            // K4 credits from the symmetric R: warp per row y, one neighbour
+            // z of y per lane, 32 at a time (collected in zb).
             for (;;) {
-                int j = 0;
-                if (lane == 0) j = atomicAdd(&work[0], 1);
-                j = __shfl_sync(FULL, j, 0);
-                if (j >= dp) break;
-                const unsigned *rj = R + j * W;
-                long long kj = 0;
-                for (int t = lane; t < W; t += 32) {
-                    unsigned bits = rj[t];
-                    while (bits) {
-                        const int i = t * 32 + __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const unsigned *ri = R + i * W;
+                int y = 0;
+                if (lane == 0) y = atomicAdd(&work[0], 1);
+                y = __shfl_sync(FULL, y, 0);
+                if (y >= dp) break;
+                const unsigned *ry = R + y * WP;
+                long long acc = 0;
+                auto batch = [&](int cnt) {
+                    if (lane < cnt) {
+                        const unsigned *rz = R + zb[lane] * WP;
                         int k = 0;
-                        for (int tt = i >> 5; tt < W; ++tt) k += __popc(rj[tt] & ri[tt]);
-                        if (k) {
-                            kj += k;
-                            atomicAdd(&kc[i], k);
-                        }
+                        for (int t = 0; t < W; ++t) k += __popc(ry[t] & rz[t]);
+                        acc += k;
                     }
-                }
-                kj = warp_sum(kj);
-                if (lane == 0 && kj) {
-                    atomicAdd(&kc[j], (int)kj);
-                    ku += kj;
-                }
-            }
-            // Columns: C[x] = rows j with x in R[j], built with ballots; each
-            // j in C[x] closes popc(R[j] & C[x]) K4s with x as the fourth.
-            unsigned *col = colbuf + wid * COLW;
-            for (;;) {
-                int x = 0;
-                if (lane == 0) x = atomicAdd(&work[1], 1);
-                x = __shfl_sync(FULL, x, 0);
-                if (x >= dp) break;
+                };
+                int nb = 0;   // entries waiting in zb (warp-uniform)
                 for (int t = 0; t < W; ++t) {
-                    const int j = t * 32 + lane;
-                    const bool bit = j < dp && ((R[j * W + (x >> 5)] >> (x & 31)) & 1u);
-                    const unsigned c = __ballot_sync(FULL, bit);
-                    if (lane == 0) col[t] = c;
-                }
-                __syncwarp();
-                long long kx = 0;
-                for (int t = lane; t < W; t += 32) {
-                    unsigned bits = col[t];
-                    while (bits) {
-                        const int j = t * 32 + __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        const unsigned *rj = R + j * W;
-                        int k = 0;
-                        for (int tt = j >> 5; tt < W; ++tt) k += __popc(rj[tt] & col[tt]);
-                        kx += k;
+                    const bool set = (ry[t] >> lane) & 1u;
+                    const unsigned bal = __ballot_sync(FULL, set);
+                    if (set) zb[nb + __popc(bal & lanemask_lt())] = (unsigned short)(t * 32 + lane);
+                    nb += __popc(bal);
+                    __syncwarp();
+                    if (nb >= 32) {
+                        batch(32);
+                        __syncwarp();
+                        if (lane < nb - 32) zb[lane] = zb[32 + lane];
+                        nb -= 32;
+                        __syncwarp();
                     }
                 }
-                kx = warp_sum(kx);
-                if (lane == 0 && kx) atomicAdd(&kc[x], (int)kx);
+                if (nb) batch(nb);
+                acc = warp_sum(acc) / 2;   // K4s of u through y
+                if (lane == 0 && acc) {
+                    kc[y] = (int)acc;
+                    atomicAdd((unsigned long long *)ksum, (unsigned long long)acc);
+                }
                 __syncwarp();
             }
         }
         __syncthreads();
         ku = warp_sum(ku);
         if (lane == 0 && ku) add64(&vacc[u].K4, ku);
+        if (use_bits && threadIdx.x == 0 && *ksum) add64(&vacc[u].K4, *ksum / 3);   // each K4 at 3 of N+(u)
         for (int i = threadIdx.x; i < nloc; i += TC_THREADS)
             if (kc[i]) add64(&vacc[g.ncol[s + i]].K4, kc[i]);
         __syncthreads();
