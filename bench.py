@@ -92,7 +92,7 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     mid = live & ~warp & ~midp & (w_root <= 3072)
     cta = live & ~warp & ~midp & ~mid & (w_root <= 12288)
     tiers = {"k_c4_warp": warp, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
-             "k_c4_global": live & (w_root > 12288)}
+             "k_c4_team": live & (w_root > 12288)}
     w_c4 = int(w_root.sum())
     res = {"B_csr": 4 * (n + 1) + 4 * m, "B_tri": b_tri, "B_c4": 4 * w_c4, "W_c4": w_c4, "B_out": 120 * n,
            "tri_probes": b_tri // 4}

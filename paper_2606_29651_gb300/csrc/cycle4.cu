@@ -21,6 +21,8 @@
 // bits, usable while UB < 2^cb - 1), which holds twice the keys in the same
 // space. Each table is emptied once per CTA; afterwards a root empties only
 // the slots it filled (kept in a 16-bit `touched` list).
+#include <cooperative_groups.h>
+
 #include "kernels.h"
 
 namespace niorca {
@@ -34,7 +36,9 @@ constexpr int CM_MAXUB = 3072;      // split; 6144 when packed
 constexpr int CC_THREADS = 512;
 constexpr int CC_SLOTS = 16384;     // split
 constexpr int CC_MAXUB = 12288;
-constexpr int CG_THREADS = 1024;
+constexpr int CT_THREADS = 1024;   // team tier: CTAs of a cluster share one dense row
+constexpr int CT_CLUSTER = 8;
+constexpr int CT_TICKETS = 4;      // chunk tickets per team (3 used)
 constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
@@ -357,68 +361,99 @@ __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, const int *wlen,
     c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, wlen, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
 }
 
-// Zero the dense rows of the global tier (only when that tier has work).
-__global__ void k_c4_zero_dense(int *dense, long long n, int slots, const int *counters) {
-    const int nh = counters[CNT_C4_GLOBAL];
-    if (nh == 0) return;
-    const long long rows = nh < slots ? nh : slots;
-    const long long total = rows * n;
+// Zero the dense rows of the team tier and their chunk tickets (only when
+// that tier has work). `words` = rows * n + CT_TICKETS * rows.
+__global__ void k_c4_zero_dense(int *dense, long long words, const int *counters) {
+    if (counters[CNT_C4_GLOBAL] == 0) return;
     int4 *d4 = reinterpret_cast<int4 *>(dense);
-    const long long n4 = total / 4;
+    const long long n4 = words / 4;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
         d4[i] = make_int4(0, 0, 0, 0);
-    for (long long i = n4 * 4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+    for (long long i = n4 * 4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words;
          i += (long long)gridDim.x * blockDim.x)
         dense[i] = 0;
 }
 
-// One CTA per root with UB > CC_MAXUB: counts in a dense global row of n ints.
+// Roots with W > CC_MAXUB: one cluster of CT_CLUSTER CTAs per root, counting
+// in a dense row of n ints in global memory that the cluster shares, so
+// that only one row per cluster is live and the rows stay in L2. Every warp
+// of the cluster takes chunks of 32 in-neighbours from a ticket counter.
 // Pass 1 adds every wedge; pass 2 reads each count (per middle vertex) and
 // marks the key with the sign bit, so that exactly one visitor credits
-// C(c, 2) to w; pass 3 stores zeros back.
-__global__ void __launch_bounds__(CG_THREADS) k_c4_global(Graph g, const int *wlen, VAcc *vacc, const int *lists,
-                                                          const int *counters, int *dense, int slots) {
-    constexpr int NW = CG_THREADS / 32;
+// C(c, 2) to w; pass 3 stores zeros back. Cluster barriers separate the
+// passes; the cluster leader resets a ticket once the pass that used it is
+// over (two barriers before its next use).
+__global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
+    k_c4_team(Graph g, const int *wlen, VAcc *vacc, const int *lists, const int *counters, int *dense, int teams) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    constexpr int NW = CT_THREADS / 32;
     __shared__ SegTab segs[NW];
     __shared__ long long pvs[NW][32];
-    if ((int)blockIdx.x >= slots) return;
-    int *row = dense + (size_t)blockIdx.x * g.n;
+    const int team = blockIdx.x / CT_CLUSTER;
+    const bool leader = cluster.block_rank() == 0 && threadIdx.x == 0;
+    int *row = dense + (size_t)team * g.n;
+    int *tickets = dense + (size_t)teams * g.n + CT_TICKETS * team;
     const int wid = threadIdx.x >> 5, lane = lane_id();
     SegTab &seg = segs[wid];
     long long *pv = pvs[wid];
     const int *glob_list = lists + 4 * (size_t)g.n;
     const int nh = counters[CNT_C4_GLOBAL];
-    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+    for (int h = team; h < nh; h += teams) {
         const int u = glob_list[h];
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
-        pv[lane] = 0;
-        walk_wedges(g, wlen, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); },
-                    [&](int) {});
-        __syncthreads();
+        const int nch = (din + 31) >> 5;
+        // chunks from ticket t until none is left: f(act, q, w) per wedge, done(v) per chunk
+        auto pass = [&](int t, auto f, auto done) {
+            for (;;) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(&tickets[t], 1);
+                c = __shfl_sync(FULL, c, 0);
+                if (c >= nch) break;
+                int v, len, pre;
+                const int total = wedge_chunk(g, wlen, b, din, c * 32, seg, v, len, pre);
+                seg_visit<4>(g.ncol, seg, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
+                __syncwarp();
+                done(v);
+                __syncwarp();
+            }
+        };
+        pass(0, [&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); }, [](int) {});
+        cluster.sync();
+        if (leader) atomicExch(&tickets[0], 0);
         long long su = 0;
-        walk_wedges(g, wlen, b, din, wid, NW, seg,
-                    [&](bool act, int q, int w) {
-                        if (!act) return;
-                        const int old = atomicOr(&row[w], (int)0x80000000);
-                        const int c = old & 0x7fffffff;
-                        if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
-                        if (old >= 0 && c >= 2) {   // first visitor of this key
-                            su += c2(c);
-                            add64(&vacc[w].C4, c2(c));
-                        }
-                    },
-                    [&](int v) {
-                        const long long x = pv[lane];
-                        if (x) add64(&vacc[v].C4, x);
-                        pv[lane] = 0;
-                    });
+        pv[lane] = 0;
+        __syncwarp();
+        pass(1,
+             [&](bool act, int q, int w) {
+                 if (!act) return;
+                 const int old = atomicOr(&row[w], (int)0x80000000);
+                 const int c = old & 0x7fffffff;
+                 if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
+                 if (old >= 0 && c >= 2) {   // first visitor of this key
+                     su += c2(c);
+                     add64(&vacc[w].C4, c2(c));
+                 }
+             },
+             [&](int v) {
+                 const long long x = pv[lane];
+                 if (x) add64(&vacc[v].C4, x);
+                 pv[lane] = 0;
+             });
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
-        __syncthreads();
-        walk_wedges(g, wlen, b, din, wid, NW, seg, [&](bool act, int, int w) { if (act) row[w] = 0; }, [&](int) {});
-        __syncthreads();
+        cluster.sync();
+        if (leader) atomicExch(&tickets[1], 0);
+        pass(2, [&](bool act, int, int w) { if (act) row[w] = 0; }, [](int) {});
+        cluster.sync();
+        if (leader) atomicExch(&tickets[2], 0);
     }
+}
+
+int c4_team_rows(int num_sms) {
+    const int t = num_sms / CT_CLUSTER;
+    return t < 1 ? 1 : t;
 }
 
 // Count bits of a packed table for ids below n: the key takes bits(n - 1).
@@ -443,10 +478,11 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
     if (w.c4slots > 0) {
-        k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, w.n, w.c4slots, w.counters);
+        const long long words = (long long)w.c4slots * w.n + (long long)CT_TICKETS * w.c4slots;
+        k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, words, w.counters);
         after_launch(st, K_C4_ZERO);
-        k_c4_global<<<w.c4slots, CG_THREADS, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, w.c4dense,
-                                                      w.c4slots);
+        k_c4_team<<<w.c4slots * CT_CLUSTER, CT_THREADS, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, w.c4dense,
+                                                                 w.c4slots);
         after_launch(st, K_C4_GLOBAL);
     }
 }

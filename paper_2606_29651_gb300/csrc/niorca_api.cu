@@ -37,7 +37,7 @@ thread_local Timeline *t_cur = nullptr;
 const char *const kNames[K_COUNT] = {
     "k_class_hist", "k_scan", "k_class_scatter", "k_relabel_rows_warp", "k_relabel_rows_cta", "k_batch_setup",
     "k_tri_warp", "k_tri_cta", "k_agg_warp", "k_agg_cta", "k_c4_warp", "k_c4_cta", "k_c4_zero_dense",
-    "k_c4_global", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big"};
+    "k_c4_team", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big"};
 }  // namespace
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
@@ -141,9 +141,9 @@ struct Layout {
 Layout plan(long long n, long long m, int num_sms, bool batch) {
     Layout L;
     L.ntiles = (int)((n + RL_TILE - 1) / RL_TILE);
-    // the dense 4-cycle rows are only reachable by a root whose wedge bound
-    // exceeds 12288, which needs m above that; one row per SM
-    L.c4slots = m > 12288 ? (num_sms < C4_SLOTS_MAX ? num_sms : C4_SLOTS_MAX) : 0;
+    // the dense 4-cycle rows are only reachable by a root with more than
+    // 12288 wedges, which needs m above that; one row per team of CTAs
+    L.c4slots = m > 12288 ? c4_team_rows(num_sms) : 0;
     const long long nt = L.ntiles;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + (bytes ? bytes : 1)); return at; };
@@ -161,7 +161,7 @@ Layout plan(long long n, long long m, int num_sms, bool batch) {
     L.scan_part = take(4 * (sp1 > sp2 ? sp1 : sp2));
     L.lists = take(4 * 6 * n);
     L.counters = take(4 * 16);
-    L.c4dense = take(4 * (size_t)L.c4slots * n);
+    L.c4dense = take(4 * c4_dense_words(L.c4slots, n));
     L.vrange = batch ? take(8 * n) : 0;
     L.total = o;
     return L;
