@@ -38,7 +38,8 @@ constexpr int CC_SLOTS = 16384;     // split
 constexpr int CC_MAXUB = 12288;
 constexpr int CT_THREADS = 1024;   // team tier: CTAs of a cluster share one dense row
 constexpr int CT_CLUSTER = 8;
-constexpr int CT_TICKETS = 4;      // chunk tickets per team (3 used)
+constexpr int CT_MAXCH = (1 << 20) / 32;   // chunks of 32 in-neighbours (degree <= 2^20)
+constexpr size_t CT_SMEM = (size_t)(CT_MAXCH + 1) * 4;
 constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
@@ -361,8 +362,7 @@ __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, const int *wlen,
     c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, wlen, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
 }
 
-// Zero the dense rows of the team tier and their chunk tickets (only when
-// that tier has work). `words` = rows * n + CT_TICKETS * rows.
+// Zero the dense rows of the team tier (only when that tier has work).
 __global__ void k_c4_zero_dense(int *dense, long long words, const int *counters) {
     if (counters[CNT_C4_GLOBAL] == 0) return;
     int4 *d4 = reinterpret_cast<int4 *>(dense);
@@ -376,25 +376,30 @@ __global__ void k_c4_zero_dense(int *dense, long long words, const int *counters
 
 // Roots with W > CC_MAXUB: one cluster of CT_CLUSTER CTAs per root, counting
 // in a dense row of n ints in global memory that the cluster shares, so
-// that only one row per cluster is live and the rows stay in L2. Every warp
-// of the cluster takes chunks of 32 in-neighbours from a ticket counter.
+// that only one row per cluster is live. The root's wedges, in the order
+// of its in-neighbours, are cut into equal slices, one per warp of the
+// cluster; every CTA keeps the prefix sums of the wedge counts of the
+// root's 32-in-neighbour chunks (W < 2^31: a root's wedges are entries of
+// rows of the CSR) to find where a slice starts.
 // Pass 1 adds every wedge; pass 2 reads each count (per middle vertex) and
 // marks the key with the sign bit, so that exactly one visitor credits
 // C(c, 2) to w; pass 3 stores zeros back. Cluster barriers separate the
-// passes; the cluster leader resets a ticket once the pass that used it is
-// over (two barriers before its next use).
+// passes.
 __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
     k_c4_team(Graph g, const int *wlen, VAcc *vacc, const int *lists, const int *counters, int *dense, int teams) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     constexpr int NW = CT_THREADS / 32;
+    constexpr int SLICES = NW * CT_CLUSTER;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    int *P = reinterpret_cast<int *>(dsm);   // chunk prefix sums, CT_MAXCH + 1
     __shared__ SegTab segs[NW];
     __shared__ long long pvs[NW][32];
+    __shared__ int wsum[NW];
     const int team = blockIdx.x / CT_CLUSTER;
-    const bool leader = cluster.block_rank() == 0 && threadIdx.x == 0;
-    int *row = dense + (size_t)team * g.n;
-    int *tickets = dense + (size_t)teams * g.n + CT_TICKETS * team;
     const int wid = threadIdx.x >> 5, lane = lane_id();
+    const int slice = (int)cluster.block_rank() * NW + wid;
+    int *row = dense + (size_t)team * g.n;
     SegTab &seg = segs[wid];
     long long *pv = pvs[wid];
     const int *glob_list = lists + 4 * (size_t)g.n;
@@ -404,50 +409,83 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
         const int4 ru = g.rinfo[u];
         const int b = ru.x, din = ru.y - ru.x;
         const int nch = (din + 31) >> 5;
-        // chunks from ticket t until none is left: f(act, q, w) per wedge, done(v) per chunk
-        auto pass = [&](int t, auto f, auto done) {
-            for (;;) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(&tickets[t], 1);
-                c = __shfl_sync(FULL, c, 0);
-                if (c >= nch) break;
+        // wedges per chunk (P[c]), then an exclusive scan in place: each
+        // thread owns a run of consecutive chunks, and only it touches them
+        for (int c = wid; c < nch; c += NW) {
+            const int p = c * 32 + lane;
+            const int l = p < din ? wedge_len(wlen, b + p, g.rinfo[g.ncol[b + p]]) : 0;
+            const int sum = warp_sum(l);
+            if (lane == 0) P[c] = sum;
+        }
+        __syncthreads();
+        {
+            const int per = (nch + CT_THREADS - 1) / CT_THREADS;
+            const int c0 = min(threadIdx.x * per, nch), c1 = min(c0 + per, nch);
+            int run = 0;
+            for (int c = c0; c < c1; ++c) run += P[c];
+            const int incl = warp_inclusive_scan(run);
+            if (lane == 31) wsum[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                const int x = wsum[lane];
+                wsum[lane] = warp_inclusive_scan(x) - x;
+            }
+            __syncthreads();
+            int acc = wsum[wid] + incl - run;
+            for (int c = c0; c < c1; ++c) {
+                const int t = P[c];
+                P[c] = acc;
+                acc += t;
+            }
+            if (c0 < c1 && c1 == nch) P[nch] = acc;   // W
+        }
+        __syncthreads();
+        const int W = P[nch];
+        const int lo = (int)((long long)W * slice / SLICES), hi = (int)((long long)W * (slice + 1) / SLICES);
+        // chunks overlapping [lo, hi): f(act, q, w) per wedge, done(v) per chunk
+        auto pass = [&](auto f, auto done) {
+            if (lo >= hi) return;
+            int c = 0, top = nch;   // last chunk with P[c] <= lo
+            while (top - c > 1) {
+                const int mid = (c + top) >> 1;
+                if (P[mid] <= lo) c = mid; else top = mid;
+            }
+            for (; c < nch && P[c] < hi; ++c) {
                 int v, len, pre;
                 const int total = wedge_chunk(g, wlen, b, din, c * 32, seg, v, len, pre);
-                seg_visit<4>(g.ncol, seg, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
+                const int from = max(lo - P[c], 0), to = min(hi - P[c], total);
+                seg_visit<4>(g.ncol, seg, pre, len, to, from, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
                 __syncwarp();
                 done(v);
                 __syncwarp();
             }
         };
-        pass(0, [&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); }, [](int) {});
+        pass([&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); }, [](int) {});
         cluster.sync();
-        if (leader) atomicExch(&tickets[0], 0);
         long long su = 0;
         pv[lane] = 0;
         __syncwarp();
-        pass(1,
-             [&](bool act, int q, int w) {
-                 if (!act) return;
-                 const int old = atomicOr(&row[w], (int)0x80000000);
-                 const int c = old & 0x7fffffff;
-                 if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
-                 if (old >= 0 && c >= 2) {   // first visitor of this key
-                     su += c2(c);
-                     add64(&vacc[w].C4, c2(c));
-                 }
-             },
-             [&](int v) {
-                 const long long x = pv[lane];
-                 if (x) add64(&vacc[v].C4, x);
-                 pv[lane] = 0;
-             });
+        pass(
+            [&](bool act, int q, int w) {
+                if (!act) return;
+                const int old = atomicOr(&row[w], (int)0x80000000);
+                const int c = old & 0x7fffffff;
+                if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
+                if (old >= 0 && c >= 2) {   // first visitor of this key
+                    su += c2(c);
+                    add64(&vacc[w].C4, c2(c));
+                }
+            },
+            [&](int v) {
+                const long long x = pv[lane];
+                if (x) add64(&vacc[v].C4, x);
+                pv[lane] = 0;
+            });
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
         cluster.sync();
-        if (leader) atomicExch(&tickets[1], 0);
-        pass(2, [&](bool act, int, int w) { if (act) row[w] = 0; }, [](int) {});
+        pass([&](bool act, int, int w) { if (act) row[w] = 0; }, [](int) {});
         cluster.sync();
-        if (leader) atomicExch(&tickets[2], 0);
     }
 }
 
@@ -478,11 +516,11 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
     if (w.c4slots > 0) {
-        const long long words = (long long)w.c4slots * w.n + (long long)CT_TICKETS * w.c4slots;
+        const long long words = (long long)c4_dense_words(w.c4slots, w.n);
         k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, words, w.counters);
         after_launch(st, K_C4_ZERO);
-        k_c4_team<<<w.c4slots * CT_CLUSTER, CT_THREADS, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, w.c4dense,
-                                                                 w.c4slots);
+        k_c4_team<<<w.c4slots * CT_CLUSTER, CT_THREADS, CT_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
+                                                                       w.c4dense, w.c4slots);
         after_launch(st, K_C4_GLOBAL);
     }
 }
@@ -491,6 +529,7 @@ void configure_cycle4() {
     cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_midp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM);
+    cudaFuncSetAttribute(k_c4_team, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT_SMEM);
 }
 
 }  // namespace niorca

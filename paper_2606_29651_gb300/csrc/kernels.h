@@ -23,7 +23,7 @@ struct Work {
     int *scan_part = nullptr;// scan block partials
     int *lists = nullptr;    // heavy-vertex lists, 6 x n
     int *counters = nullptr; // list lengths and flags, 16 ints
-    int *c4dense = nullptr;  // dense counting rows for the largest 4-cycle roots, then 4 tickets per row
+    int *c4dense = nullptr;  // dense counting rows for the largest 4-cycle roots
     int c4slots = 0;         // rows in c4dense (each n ints), one per team of CTAs
     int *status = nullptr;   // device status word (not part of the carve)
     int num_sms = 0;
@@ -54,10 +54,9 @@ enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_GLOBAL = 3, 
 constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
 constexpr int SCAN_TILE = 4096;      // elements per scan block
 constexpr int LONG_ROW_CLASS = 32;   // deg_class(512): rows from here on get a CTA each
-// Dense rows (one per cluster of CTAs) of the largest 4-cycle tier; each
-// row is n ints, followed by 4 ints of tickets per row.
+// Dense rows (one per cluster of CTAs) of the largest 4-cycle tier, n ints each.
 int c4_team_rows(int num_sms);
-inline size_t c4_dense_words(long long rows, long long n) { return (size_t)(rows * n + 4 * rows); }
+inline size_t c4_dense_words(long long rows, long long n) { return (size_t)(rows * n); }
 
 size_t scan_partials(long long len);
 void launch_exclusive_scan(const int *in, int *out, long long len, bool write_total, int *part,
