@@ -74,12 +74,24 @@ __device__ __forceinline__ int wedge_chunk(const Graph &g, const int *wlen, int 
 // per chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...): f(act, q, w) on
 // every lane, act meaning that w is a wedge end through the v owned by lane
 // q; then done(v) per chunk.
+// A root with at most 32 in-neighbours has one chunk; its table may be
+// built already (built = true: T holds it, v/len/pre/total are the lane's).
+struct Chunk0 {
+    bool built;
+    int v, len, pre, total;
+};
+
 template <class F, class D>
 __device__ __forceinline__ void walk_wedges(const Graph &g, const int *wlen, int b, int din, int c0, int cstep,
-                                            SegTab &T, F f, D done) {
+                                            SegTab &T, F f, D done, Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
-        int v, len, pre;
-        const int total = wedge_chunk(g, wlen, b, din, cb, T, v, len, pre);
+        int v, len, pre, total;
+        if (c0pre.built) {
+            v = c0pre.v, len = c0pre.len, pre = c0pre.pre, total = c0pre.total;
+            c0pre.built = false;
+        } else {
+            total = wedge_chunk(g, wlen, b, din, cb, T, v, len, pre);
+        }
         seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
         __syncwarp();
         done(v);
@@ -185,7 +197,7 @@ struct PackedTab {
 template <bool CTA, class Tab>
 __device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *vacc, int u, int b, int din,
                                         const Tab &T, int wid, int nw, int tid, int nthreads, SegTab &seg,
-                                        long long *pv, int *flags) {
+                                        long long *pv, int *flags, Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
     const int lane = lane_id();
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
@@ -210,7 +222,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *v
         }
     };
     if (CTA) walk_wedges_cta<false>(g, wlen, b, din, wid, nw, seg, insert, [](int) {});
-    else walk_wedges(g, wlen, b, din, 0, 1, seg, insert, [](int) {});
+    else walk_wedges(g, wlen, b, din, 0, 1, seg, insert, [](int) {}, c0pre);
     sync();
     const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
     if (CTA ? flags[1] != 0 : __any_sync(FULL, dup_l)) {
@@ -281,8 +293,15 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *w
         const int b = ru.x, din = ru.y - ru.x;
         if (din < 2) continue;
         long long ub = 0;   // exact wedge count W of root u
-        for (int p = lane; p < din; p += 32) ub += wedge_len(wlen, b + p, g.rinfo[g.ncol[b + p]]);
-        ub = warp_sum(ub);
+        Chunk0 c0pre{false, 0, 0, 0, 0};
+        if (din <= 32) {   // one chunk: its segment table gives W
+            c0pre.total = wedge_chunk(g, wlen, b, din, 0, S.seg, c0pre.v, c0pre.len, c0pre.pre);
+            c0pre.built = true;
+            ub = c0pre.total;
+        } else {
+            for (int p = lane; p < din; p += 32) ub += wedge_len(wlen, b + p, g.rinfo[g.ncol[b + p]]);
+            ub = warp_sum(ub);
+        }
         if (ub < 2) continue;
         if (ub > maxub || ub > pack_lim) {
             if (lane == 0) {
@@ -299,7 +318,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *w
         unsigned slots = next_pow2(2 * (unsigned)ub);
         slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
         const PackedTab T{S.t, slots - 1, cb, nullptr};
-        c4_root<false>(g, wlen, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr);
+        c4_root<false>(g, wlen, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
     }
 }
 
