@@ -478,8 +478,8 @@ def run_serve(args) -> None:
     total_edges = sum(len(c) // 2 for _, c in graphs)
     budget = args.serve_budget_gb << 30
     with Server(0, mem_budget=budget) as srv:          # capacity: everything submitted at once
-        for rp, ci in graphs[:8]:
-            srv.submit(rp, ci).result()
+        for f in [srv.submit(rp, ci) for rp, ci in graphs]:   # warm-up pass: staging buffers reach size
+            f.result()
         t0 = time.perf_counter()
         futs = [srv.submit(rp, ci) for rp, ci in graphs]
         for f in futs:

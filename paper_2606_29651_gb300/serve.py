@@ -46,10 +46,29 @@ def footprint(num_graphs: int, total_n: int, total_m: int) -> int:
     return io + _lib.batch_workspace_bytes(num_graphs, total_n, total_m)
 
 
-class _Batch:
-    def __init__(self, reqs, stream, nbytes):
-        self.reqs = reqs
+class _Slot:
+    """A stream and its pinned host staging buffers, kept from batch to batch
+    (pinning memory is far slower than copying into it); a buffer grows by
+    half again when a batch needs more."""
+
+    def __init__(self, stream):
         self.stream = stream
+        self._bufs = {}
+
+    def host(self, name: str, numel: int, dtype) -> torch.Tensor:
+        buf = self._bufs.get(name)
+        if buf is None or buf.numel() < numel:
+            size = max(numel, int(1.5 * buf.numel()) if buf is not None else numel, 1)
+            buf = torch.empty(size, dtype=dtype).pin_memory()
+            self._bufs[name] = buf
+        return buf[:numel]
+
+
+class _Batch:
+    def __init__(self, reqs, slot, nbytes):
+        self.reqs = reqs
+        self.slot = slot
+        self.stream = slot.stream
         self.nbytes = nbytes
         self.event = torch.cuda.Event()
         self.host_out = None
@@ -67,9 +86,9 @@ class Server:
         self.max_batch_edges = int(max_batch_edges)
         with torch.cuda.device(self.device):
             self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
+        self._free_slots = [_Slot(st) for st in self.streams]
         self._pending: collections.deque = collections.deque()
         self._inflight: list[_Batch] = []
-        self._free_streams = list(self.streams)
         self._in_use = 0
         self._cv = threading.Condition()
         self._stop = False
@@ -123,8 +142,9 @@ class Server:
         return take, footprint(len(take), n, m) if take else 0
 
     def _launch(self, reqs, nbytes):
-        stream = self._free_streams.pop()
-        b = _Batch(reqs, stream, nbytes)
+        slot = self._free_slots.pop()
+        stream = slot.stream
+        b = _Batch(reqs, slot, nbytes)
         ns = np.array([r.n for r in reqs], dtype=np.int64)
         ms = np.array([r.m for r in reqs], dtype=np.int64)
         vo = np.zeros(len(reqs) + 1, dtype=np.int64)
@@ -132,15 +152,16 @@ class Server:
         vo[1:] = np.cumsum(ns)
         eo[1:] = np.cumsum(ms)
         total_n, total_m = int(vo[-1]), int(eo[-1])
-        rowptr = torch.empty(total_n + 1, dtype=torch.int32).pin_memory()
-        colidx = torch.empty(max(total_m, 1), dtype=torch.int32).pin_memory()
+        rowptr = slot.host("rowptr", total_n + 1, torch.int32)
+        colidx = slot.host("colidx", max(total_m, 1), torch.int32)
+        offs = slot.host("offs", 2 * (len(reqs) + 1), torch.int64)
+        host_out = slot.host("out", total_n * 15, torch.int64).view(total_n, 15)
         rp, ci = rowptr.numpy(), colidx.numpy()
         for g, r in enumerate(reqs):
-            rp[vo[g]:vo[g + 1]] = r.rowptr[:-1] + eo[g]
+            np.add(r.rowptr[:-1], np.int32(eo[g]), out=rp[vo[g]:vo[g + 1]])
             ci[eo[g]:eo[g + 1]] = r.colidx
         rp[-1] = total_m
-        offs = torch.from_numpy(np.concatenate([vo, eo])).pin_memory()
-        host_out = torch.empty((total_n, 15), dtype=torch.int64).pin_memory()
+        offs.numpy()[:] = np.concatenate([vo, eo])
         with torch.cuda.stream(stream):
             d_rp = rowptr.to(self.device, non_blocking=True)
             d_ci = colidx[:total_m].to(self.device, non_blocking=True)
@@ -150,7 +171,7 @@ class Server:
             host_out.copy_(out, non_blocking=True)
             b.event.record(stream)
         b.host_out = host_out
-        b.keep = (rowptr, colidx, offs, d_rp, d_ci, d_off, out, vo)
+        b.keep = (d_rp, d_ci, d_off, out, vo)
         self._in_use += nbytes
         self._inflight.append(b)
         self.batches += 1
@@ -171,7 +192,7 @@ class Server:
                 r.future.set_result(res[vo[g]:vo[g + 1]].copy())
         self.completed += len(b.reqs)
         self._in_use -= b.nbytes
-        self._free_streams.append(b.stream)
+        self._free_slots.append(b.slot)
         b.keep = None
 
     def _loop(self):
@@ -189,7 +210,7 @@ class Server:
                 self._retire(b, now)
             launched = False
             with self._cv:
-                if self._pending and self._free_streams:
+                if self._pending and self._free_slots:
                     reqs, nbytes = self._admit()
                 else:
                     reqs, nbytes = [], 0
