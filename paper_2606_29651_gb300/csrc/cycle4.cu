@@ -11,8 +11,7 @@
 //   u gets sum_w C(c_w, 2), w gets C(c_w, 2),
 //   each middle vertex v gets sum over its wedges of (c_w - 1).
 // The wedges through v are the entries of row v below u: a prefix of row v
-// whose length the triangle stage left at the in-entry (u, v) of `tcnt`
-// (clamped to the row, so that no input can send a read outside it). Roots
+// ending at the position of u, which a search of N+(v) finds. Roots
 // are routed by their wedge count W (a count is at most W too): one warp,
 // four warps, a 512-thread CTA, or a CTA with a dense count row in global
 // memory. Tables are open-addressing
@@ -44,18 +43,18 @@ constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
-// Wedge-segment length through the in-entry at position p of a root's row
-// (left there by the triangle stage), clamped to the row of v.
-__device__ __forceinline__ int wedge_len(const int *wlen, int p, const int4 &rv) {
-    const int l = wlen[p];
-    return l < 0 ? 0 : (l > rv.z - rv.x ? rv.z - rv.x : l);
+// Wedges u - v - w through the in-neighbour v of root u: the entries of row
+// v below u, i.e. the position of u in row v (u is in N+(v)), found by a
+// search of N+(v) whose last steps touch the lines the walk reads next.
+__device__ __forceinline__ int wedge_len(const Graph &g, int u, const int4 &rv) {
+    return lower_bound(g.ncol, rv.y, rv.z, u) - rv.x;
 }
 
 // Segment table of in-neighbour chunk cb of root u in the calling warp: the
 // wedge prefixes of the rows of v = ncol[b + cb + lane] concatenated. Returns
 // the total length; the lane's own v, segment length and offset come back in
 // v, len, pre.
-__device__ __forceinline__ int wedge_chunk(const Graph &g, const int *wlen, int b, int din, int cb, SegTab &T, int &v,
+__device__ __forceinline__ int wedge_chunk(const Graph &g, int u, int b, int din, int cb, SegTab &T, int &v,
                                            int &len, int &pre) {
     const int p = cb + lane_id();
     int st = 0;
@@ -65,7 +64,7 @@ __device__ __forceinline__ int wedge_chunk(const Graph &g, const int *wlen, int 
         v = g.ncol[b + p];
         const int4 rv = g.rinfo[v];
         st = rv.x;
-        len = wedge_len(wlen, b + p, rv);
+        len = wedge_len(g, u, rv);
     }
     return seg_build(T, st, len, pre);
 }
@@ -82,7 +81,7 @@ struct Chunk0 {
 };
 
 template <class F, class D>
-__device__ __forceinline__ void walk_wedges(const Graph &g, const int *wlen, int b, int din, int c0, int cstep,
+__device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep,
                                             SegTab &T, F f, D done, Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
     for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
         int v, len, pre, total;
@@ -90,7 +89,7 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, const int *wlen, int
             v = c0pre.v, len = c0pre.len, pre = c0pre.pre, total = c0pre.total;
             c0pre.built = false;
         } else {
-            total = wedge_chunk(g, wlen, b, din, cb, T, v, len, pre);
+            total = wedge_chunk(g, u, b, din, cb, T, v, len, pre);
         }
         seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
         __syncwarp();
@@ -103,11 +102,11 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, const int *wlen, int
 // table of each chunk and takes the windows wid, wid + nw, ... of 32
 // elements. With DONE, warp 0 calls done(v) after the CTA finished the chunk.
 template <bool DONE, class F, class D>
-__device__ __forceinline__ void walk_wedges_cta(const Graph &g, const int *wlen, int b, int din, int wid, int nw,
+__device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, int din, int wid, int nw,
                                                 SegTab &T, F f, D done) {
     for (int cb = 0; cb < din; cb += 32) {
         int v, len, pre;
-        const int total = wedge_chunk(g, wlen, b, din, cb, T, v, len, pre);
+        const int total = wedge_chunk(g, u, b, din, cb, T, v, len, pre);
         seg_visit<4>(g.ncol, T, pre, len, total, wid * 32, nw * 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
         if (DONE) {
             __syncthreads();
@@ -195,7 +194,7 @@ struct PackedTab {
 // pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
 // the CTA).
 template <bool CTA, class Tab>
-__device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *vacc, int u, int b, int din,
+__device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din,
                                         const Tab &T, int wid, int nw, int tid, int nthreads, SegTab &seg,
                                         long long *pv, int *flags, Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
     const int lane = lane_id();
@@ -221,8 +220,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *v
             T.touched[base + __popc(fresh & lanemask_lt())] = (unsigned short)slot;
         }
     };
-    if (CTA) walk_wedges_cta<false>(g, wlen, b, din, wid, nw, seg, insert, [](int) {});
-    else walk_wedges(g, wlen, b, din, 0, 1, seg, insert, [](int) {}, c0pre);
+    if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
+    else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {}, c0pre);
     sync();
     const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
     if (CTA ? flags[1] != 0 : __any_sync(FULL, dup_l)) {
@@ -251,8 +250,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, const int *wlen, VAcc *v
             if (x) add64(&vacc[v].C4, x);
             pv[lane] = 0;
         };
-        if (CTA) walk_wedges_cta<true>(g, wlen, b, din, wid, nw, seg, middle, flush);
-        else walk_wedges(g, wlen, b, din, 0, 1, seg, middle, flush);
+        if (CTA) walk_wedges_cta<true>(g, u, b, din, wid, nw, seg, middle, flush);
+        else walk_wedges(g, u, b, din, 0, 1, seg, middle, flush);
         sync();
     }
     if (CTA) {
@@ -278,7 +277,7 @@ struct __align__(16) C4WarpSmem {
 
 // One warp per root with W <= maxub (<= CW_MAXUB) that fits a packed table;
 // other roots are queued for the wider tiers.
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *wlen, VAcc *vacc, int *lists,
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists,
                                                            int *counters, int maxub, int cb) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
@@ -295,11 +294,11 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *w
         long long ub = 0;   // exact wedge count W of root u
         Chunk0 c0pre{false, 0, 0, 0, 0};
         if (din <= 32) {   // one chunk: its segment table gives W
-            c0pre.total = wedge_chunk(g, wlen, b, din, 0, S.seg, c0pre.v, c0pre.len, c0pre.pre);
+            c0pre.total = wedge_chunk(g, u, b, din, 0, S.seg, c0pre.v, c0pre.len, c0pre.pre);
             c0pre.built = true;
             ub = c0pre.total;
         } else {
-            for (int p = lane; p < din; p += 32) ub += wedge_len(wlen, b + p, g.rinfo[g.ncol[b + p]]);
+            for (int p = lane; p < din; p += 32) ub += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
             ub = warp_sum(ub);
         }
         if (ub < 2) continue;
@@ -318,7 +317,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *w
         unsigned slots = next_pow2(2 * (unsigned)ub);
         slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
         const PackedTab T{S.t, slots - 1, cb, nullptr};
-        c4_root<false>(g, wlen, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
+        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
     }
 }
 
@@ -326,7 +325,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, const int *w
 // 2 x SLOTS packed ones) lives in dynamic shared memory and is emptied once
 // per CTA.
 template <int THREADS, int SLOTS, int MAXUB, bool PACKED>
-__device__ __forceinline__ void c4_queue(const Graph &g, const int *wlen, VAcc *vacc, const int *list, int count,
+__device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count,
                                          int cb) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
@@ -350,11 +349,11 @@ __device__ __forceinline__ void c4_queue(const Graph &g, const int *wlen, VAcc *
         const int4 ru = g.rinfo[u];
         if (PACKED) {
             const PackedTab T{words, 2 * SLOTS - 1, cb, touched};
-            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
+            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
         } else {
             const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS - 1,
                              touched};
-            c4_root<true>(g, wlen, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
+            c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
         }
     }
 }
@@ -366,19 +365,19 @@ constexpr size_t cq_smem(int threads, int slots, int maxub) {
 constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXUB);
 constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXUB);
 
-__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, const int *wlen, VAcc *vacc, const int *lists,
+__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists,
                                                        const int *counters, int cb) {
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, false>(g, wlen, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
 }
 
-__global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, const int *wlen, VAcc *vacc, const int *lists,
+__global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, VAcc *vacc, const int *lists,
                                                         const int *counters, int cb) {
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, true>(g, wlen, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
 }
 
-__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, const int *wlen, VAcc *vacc, const int *lists,
+__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists,
                                                        const int *counters, int cb) {
-    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, wlen, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
+    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
 }
 
 // Zero the dense rows of the team tier (only when that tier has work).
@@ -405,7 +404,7 @@ __global__ void k_c4_zero_dense(int *dense, long long words, const int *counters
 // C(c, 2) to w; pass 3 stores zeros back. Cluster barriers separate the
 // passes.
 __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
-    k_c4_team(Graph g, const int *wlen, VAcc *vacc, const int *lists, const int *counters, int *dense, int teams) {
+    k_c4_team(Graph g, VAcc *vacc, const int *lists, const int *counters, int *dense, int teams) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     constexpr int NW = CT_THREADS / 32;
@@ -432,7 +431,7 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
         // thread owns a run of consecutive chunks, and only it touches them
         for (int c = wid; c < nch; c += NW) {
             const int p = c * 32 + lane;
-            const int l = p < din ? wedge_len(wlen, b + p, g.rinfo[g.ncol[b + p]]) : 0;
+            const int l = p < din ? wedge_len(g, u, g.rinfo[g.ncol[b + p]]) : 0;
             const int sum = warp_sum(l);
             if (lane == 0) P[c] = sum;
         }
@@ -471,7 +470,7 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
             }
             for (; c < nch && P[c] < hi; ++c) {
                 int v, len, pre;
-                const int total = wedge_chunk(g, wlen, b, din, c * 32, seg, v, len, pre);
+                const int total = wedge_chunk(g, u, b, din, c * 32, seg, v, len, pre);
                 const int from = max(lo - P[c], 0), to = min(hi - P[c], total);
                 seg_visit<4>(g.ncol, seg, pre, len, to, from, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
                 __syncwarp();
@@ -525,20 +524,20 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxub = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXUB ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXUB;
     const int cb = packed_count_bits(w.n);
-    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, maxub,
+    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxub,
                                                                          cb);
     after_launch(st, K_C4_WARP);
-    k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
+    k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MIDP);
-    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
+    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MID);
-    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, cb);
+    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
     if (w.c4slots > 0) {
         const long long words = (long long)c4_dense_words(w.c4slots, w.n);
         k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, words, w.counters);
         after_launch(st, K_C4_ZERO);
-        k_c4_team<<<w.c4slots * CT_CLUSTER, CT_THREADS, CT_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
+        k_c4_team<<<w.c4slots * CT_CLUSTER, CT_THREADS, CT_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
                                                                        w.c4dense, w.c4slots);
         after_launch(st, K_C4_GLOBAL);
     }

@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
             a.S1 = s1; a.A1 = 0; a.P6 = p6; a.A2 = 0; a.A3 = 0; a.D12 = 0; a.K4 = 0; a.C4 = 0;
             vacc[r] = a;
         }
-        for (int p = nb + lane; p < nb + d; p += 32) tcnt[p] = 0;
+        for (int p = sp + lane; p < nb + d; p += 32) tcnt[p] = 0;
         __syncwarp();
     }
     bad = __reduce_or_sync(FULL, bad);
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
         }
         __syncthreads();
         const int sp = (int)red[0][0];
-        for (int p = nb + threadIdx.x; p < nb + d; p += RLC_THREADS) tcnt[p] = 0;
+        for (int p = sp + threadIdx.x; p < nb + d; p += RLC_THREADS) tcnt[p] = 0;
         __syncthreads();
     }
     if (bad) set_status(status, bad);

@@ -45,20 +45,12 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    // Wedge lengths for the 4-cycle stage: for the out-neighbour x = N+(u)[j]
-    // of u, the entries of row u below x number (s - ru.x) + j; they are
-    // stored at the in-entry of u in row x (a slot of tcnt that t does not
-    // use), found by a search of N-(x).
-    auto wedge_length = [&](int u, const int4 &ru, int j, const int4 &rx) {
-        const int q = lower_bound(g.ncol, rx.x, rx.y, u);
-        if (q < rx.y && g.ncol[q] == u) tcnt[q] = (ru.y - ru.x) + j;
-    };
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
-        if (dp < 2 || dp > maxd) {
-            for (int j = lane; j < dp; j += 32) wedge_length(u, ru, j, g.rinfo[g.ncol[s + j]]);
-            if (dp > maxd && lane == 0) {
+        if (dp < 2) continue;
+        if (dp > maxd) {
+            if (lane == 0) {
                 if (dp <= TS_MAXD) heavy[atomicAdd(&counters[CNT_TRI_HEAVY], 1)] = u;
                 else heavy[g.n - 1 - atomicAdd(&counters[CNT_TRI_BIG], 1)] = u;
             }
@@ -77,14 +69,13 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
         const int umax = g.ncol[e - 1];
         __syncwarp();
         int found = 0;
-        for (int jb = 0; jb < dp; jb += 32) {   // the last out-neighbour has no row to walk
+        for (int jb = 0; jb < dp - 1; jb += 32) {   // the last out-neighbour has no row to walk
             const int j = jb + lane;
             int len = 0, vs = 0;
-            int4 rv = make_int4(0, 0, 0, 0);
-            if (j < dp) {
-                rv = g.rinfo[g.ncol[s + j]];
+            if (j < dp - 1) {
+                const int4 rv = g.rinfo[g.ncol[s + j]];
                 vs = rv.y;
-                len = j < dp - 1 ? rv.z - rv.y : 0;
+                len = rv.z - rv.y;
             }
             int mypre;
             const int total = seg_build(S.seg, vs, len, mypre);
@@ -106,7 +97,6 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
                 }
             });
             __syncwarp();
-            if (j < dp) wedge_length(u, ru, j, rv);   // row x_j was just read: its N- is near
         }
         if (!__any_sync(FULL, found)) continue;
         for (int i = lane; i < dp; i += 32)
@@ -343,8 +333,6 @@ __global__ void __launch_bounds__(TB_THREADS) k_tri_big(Graph g, int *tcnt, VAcc
 void launch_stage1(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxd = w.tune[TUNE_WARP_MAXD] < TW_MAXD ? w.tune[TUNE_WARP_MAXD] : TW_MAXD;
-    // (k_tri_warp also leaves, in the in-entries of tcnt, the wedge lengths
-    // that the 4-cycle stage reads)
     k_tri_warp<<<w.num_sms * w.tune[TUNE_GRID_TRI], TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
                                                                           maxd);
     after_launch(st, K_TRI_WARP);
