@@ -27,10 +27,8 @@
 namespace niorca {
 
 constexpr int CW_WARPS = 4;
-constexpr int CW_SLOTS = 2048;      // packed (k_c4_warpl)
+constexpr int CW_SLOTS = 2048;      // packed
 constexpr int CW_MAXUB = 1536;
-constexpr int CW_SMALL_SLOTS = 1024;   // packed (k_c4_warp)
-constexpr int CW_SMALL = 512;          // largest W counted by k_c4_warp
 constexpr int CM_THREADS = 128;
 constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
 constexpr int CM_MAXUB = 3072;      // split; 6144 when packed
@@ -271,38 +269,23 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
 
 constexpr int CW_MIN_SLOTS = 64;
 
-template <int SLOTS>
 struct __align__(16) C4WarpSmem {
-    unsigned t[SLOTS];
+    unsigned t[CW_SLOTS];
     SegTab seg;
     long long pv[32];
 };
 
-// Counts root u in the calling warp with a packed table of at least 2W
-// slots (at most SLOTS; W <= 3/4 of SLOTS), prebuilt first chunk optional.
-template <int SLOTS>
-__device__ __forceinline__ void c4_warp_root(const Graph &g, VAcc *vacc, C4WarpSmem<SLOTS> &S, int u, int b, int din,
-                                             long long W, int cb, Chunk0 c0pre) {
-    unsigned slots = next_pow2(2 * (unsigned)W);
-    slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > SLOTS ? SLOTS : slots);
-    const PackedTab T{S.t, slots - 1, cb, nullptr};
-    c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane_id(), 32, S.seg, S.pv, nullptr, c0pre);
-}
-
-// Every root, one warp each: those with W <= CW_SMALL (most) are counted
-// here with 1024-slot tables, which leave room for many warps per SM; roots
-// up to maxub (<= CW_MAXUB) that fit a packed table go to k_c4_warpl, the
-// rest are queued for the CTA tiers.
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters, int maxub,
-                                                           int cb) {
-    __shared__ C4WarpSmem<CW_SMALL_SLOTS> sm_all[CW_WARPS];
-    C4WarpSmem<CW_SMALL_SLOTS> &S = sm_all[threadIdx.x >> 5];
+// One warp per root with W <= maxub (<= CW_MAXUB) that fits a packed table;
+// other roots are queued for the wider tiers.
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists,
+                                                           int *counters, int maxub, int cb) {
+    __shared__ C4WarpSmem sm_all[CW_WARPS];
+    C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
-    const int small = maxub < CW_SMALL ? maxub : CW_SMALL;
-    PackedTab{S.t, CW_SMALL_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
+    PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
     __syncwarp();
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
@@ -319,11 +302,10 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             ub = warp_sum(ub);
         }
         if (ub < 2) continue;
-        if (ub > small || ub > pack_lim) {
+        if (ub > maxub || ub > pack_lim) {
             if (lane == 0) {
                 int which, list;   // queue counter and list slot (lists + list * n)
-                if (ub <= maxub && ub <= pack_lim) { which = CNT_C4_WARPL; list = 6; }
-                else if (ub > CC_MAXUB) { which = CNT_C4_GLOBAL; list = 4; }
+                if (ub > CC_MAXUB) { which = CNT_C4_GLOBAL; list = 4; }
                 else if (ub <= 2 * CM_MAXUB && ub <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
                 else if (ub <= CM_MAXUB) { which = CNT_C4_MID; list = 2; }
                 else { which = CNT_C4_CTA; list = 3; }
@@ -331,30 +313,11 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             }
             continue;
         }
-        c4_warp_root(g, vacc, S, u, b, din, ub, cb, c0pre);
-    }
-}
-
-// Queued roots with CW_SMALL < W <= maxub, one warp each, 2048-slot tables.
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warpl(Graph g, VAcc *vacc, const int *lists,
-                                                            const int *counters, int cb) {
-    __shared__ C4WarpSmem<CW_SLOTS> sm_all[CW_WARPS];
-    C4WarpSmem<CW_SLOTS> &S = sm_all[threadIdx.x >> 5];
-    const int lane = lane_id();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int *list = lists + 6 * (size_t)g.n;
-    const int nq = counters[CNT_C4_WARPL];
-    PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
-    __syncwarp();
-    for (int h = gw; h < nq; h += nw) {
-        const int u = list[h];
-        const int4 ru = g.rinfo[u];
-        const int b = ru.x, din = ru.y - ru.x;
-        long long ub = 0;
-        for (int p = lane; p < din; p += 32) ub += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
-        ub = warp_sum(ub);
-        c4_warp_root(g, vacc, S, u, b, din, ub, cb, Chunk0{false, 0, 0, 0, 0});
+        // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
+        unsigned slots = next_pow2(2 * (unsigned)ub);
+        slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
+        const PackedTab T{S.t, slots - 1, cb, nullptr};
+        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
     }
 }
 
@@ -564,8 +527,6 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxub,
                                                                          cb);
     after_launch(st, K_C4_WARP);
-    k_c4_warpl<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, cb);
-    after_launch(st, K_C4_WARPL);
     k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MIDP);
     k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
