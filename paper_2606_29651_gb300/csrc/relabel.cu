@@ -205,9 +205,12 @@ __device__ __forceinline__ long long c2m1(int d) {  // C(d - 1, 2)
     return a * (a - 1) / 2;
 }
 
-// Row relabelling, one warp per row (rows below LONG_ROW_CLASS).
+// Row relabelling, one warp per row (rows below LONG_ROW_CLASS), taken in
+// input order so that the rows are read sequentially and written scattered.
 // Pass 1 validates the row, counts its classes and sums neighbour degrees;
-// pass 2 writes every new id at its class offset (stable within a class).
+// pass 2 writes every new id at its class offset (stable within a class);
+// the first 64 entries keep their new id and class in registers between
+// the passes.
 __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, const int *colidx, int n,
                                                            const int2 *vrange, const int2 *vinfo, const int *perm,
                                                            const int *nrow, const int *coff, int ntiles, int *ncol,
@@ -216,19 +219,21 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
     __shared__ int hist_all[8][NCLASS];
     const int lane = lane_id();
     int *H = hist_all[threadIdx.x >> 5];
-    const int bound = coff[long_class * ntiles];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     int bad = 0;
-    for (int r = gw; r < bound; r += nw) {
-        const int x = perm[r];
-        const int nb = nrow[r], d = nrow[r + 1] - nb;
+    for (int x = gw; x < n; x += nw) {
+        const int2 vx = vinfo[x];   // new id, degree (0 for a row with bad offsets)
+        const int r = vx.x, d = vx.y;
+        if (deg_class(d) >= long_class) continue;   // a CTA takes it
         const int ob = d > 0 ? rowptr[x] : 0;
+        const int nb = nrow[r];
         const int2 vr = vrange ? vrange[x] : make_int2(0, n);
         for (int c = lane; c < NCLASS; c += 32) H[c] = 0;
         __syncwarp();
         long long s1 = 0, p6 = 0;
         int below = 0, last = -1;
+        int nv0 = 0, nc0 = NCLASS + lane, nv1 = 0, nc1 = NCLASS + lane;   // entries lane and 32 + lane
         for (int k = 0; k < d; k += 32) {
             const int i = k + lane;
             const bool act = i < d;
@@ -241,10 +246,13 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
                 if (ys < 0) { bad |= ST_EINVAL; ys = x; }
                 else if (ys == x || (i > 0 && y <= yp)) bad |= ST_ENOTSIMPLE;
                 const int2 vi = vinfo[ys];
-                atomicAdd(&H[deg_class(vi.y)], 1);
+                const int c = deg_class(vi.y);
+                atomicAdd(&H[c], 1);
                 s1 += vi.y;
                 p6 += c2m1(vi.y);
                 below += vi.x < r;
+                if (k == 0) { nv0 = vi.x; nc0 = c; }
+                else if (k == 32) { nv1 = vi.x; nc1 = c; }
             }
         }
         // exclusive scan of the 128 class counts: 4 per lane
@@ -262,10 +270,16 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
         for (int k = 0; k < d; k += 32) {
             const int i = k + lane;
             const bool act = i < d;
-            int ys = act ? global_id(colidx[ob + i], vr, n) : 0;
-            if (ys < 0) ys = x;
-            const int2 vi = act ? vinfo[ys] : make_int2(0, 0);
-            const int c = act ? deg_class(vi.y) : NCLASS + lane;
+            int nid, c;
+            if (k == 0) { nid = nv0; c = nc0; }
+            else if (k == 32) { nid = nv1; c = nc1; }
+            else {
+                int ys = act ? global_id(colidx[ob + i], vr, n) : 0;
+                if (ys < 0) ys = x;
+                const int2 vi = act ? vinfo[ys] : make_int2(0, 0);
+                nid = vi.x;
+                c = act ? deg_class(vi.y) : NCLASS + lane;
+            }
             const unsigned peers = __match_any_sync(FULL, c);
             const int rank = __popc(peers & lanemask_lt());
             int pos = 0;
@@ -273,7 +287,7 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
             __syncwarp();
             if (act && rank == 0) H[c] += __popc(peers);
             __syncwarp();
-            if (act) ncol[nb + pos] = vi.x;
+            if (act) ncol[nb + pos] = nid;
         }
         s1 = warp_sum(s1);
         p6 = warp_sum(p6);

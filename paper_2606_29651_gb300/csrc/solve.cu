@@ -1,7 +1,7 @@
 // solve.cu -- Stage III-b: the orbit equations (Sec. 5 and the Appendix).
 //
-// One warp per vertex x gathers, over N(x), the neighbours' S1 (sum of their
-// neighbours' degrees) and A1 (twice their triangle count); together with
+// For every vertex x the neighbours' S1 (sum of their neighbours' degrees)
+// and A1 (twice their triangle count) are summed over N(x); together with
 // x's own accumulators this gives the nine f* variables of Table 1 in closed
 // form (each is a sum over the substructures of Fig. 3 around x):
 //   f_12^14 = D12
@@ -76,32 +76,60 @@ __device__ __forceinline__ void to_induced(long long *p) {
     p[10] = i10; p[11] = i11; p[12] = i12; p[13] = i13; p[14] = i14;
 }
 
+// A warp takes 32 consecutive vertices: each lane loads its vertex's row
+// bounds, accumulators and output row up front; the warp then sums S1 and
+// A1 over the neighbours of each of the 32 vertices in turn (coalesced
+// gathers, two vertices in flight), and each lane solves and writes its own
+// vertex.
 __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const int *perm, long long *out,
                                                int induced) {
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int x = gw; x < g.n; x += nw) {
-        const int4 rx = g.rinfo[x];
-        const int b = rx.x, e = rx.z;
-        long long sS1 = 0, sA1 = 0;
-        for (int p = b + lane; p < e; p += 32) {
-            const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[p]]);
-            sS1 += sa.x;
-            sA1 += sa.y;
+    for (int x0 = gw * 32; x0 < g.n; x0 += nw * 32) {
+        const int x = x0 + lane;
+        const bool have = x < g.n;
+        int4 rx = make_int4(0, 0, 0, 0);
+        VAcc a{};
+        int px = 0;
+        if (have) {
+            rx = g.rinfo[x];
+            a = vacc[x];
+            px = perm[x];
         }
-        sS1 = warp_sum(sS1);
-        sA1 = warp_sum(sA1);
-        if (lane < 15) {
-            const VAcc a = vacc[x];
+        long long mS1 = 0, mA1 = 0;   // this lane's vertex
+        const int cnt = min(32, g.n - x0);
+        for (int k = 0; k < cnt; k += 2) {
+            const int b0 = __shfl_sync(FULL, rx.x, k), e0 = __shfl_sync(FULL, rx.z, k);
+            const int b1 = __shfl_sync(FULL, rx.x, k + 1 < 32 ? k + 1 : 31);
+            const int e1 = k + 1 < cnt ? __shfl_sync(FULL, rx.z, k + 1) : b1;
+            long long s0 = 0, t0 = 0, s1 = 0, t1 = 0;
+            for (int off = lane; off < max(e0 - b0, e1 - b1); off += 32) {
+                if (b0 + off < e0) {
+                    const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[b0 + off]]);
+                    s0 += sa.x;
+                    t0 += sa.y;
+                }
+                if (b1 + off < e1) {
+                    const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[b1 + off]]);
+                    s1 += sa.x;
+                    t1 += sa.y;
+                }
+            }
+            s0 = warp_sum(s0);
+            t0 = warp_sum(t0);
+            s1 = warp_sum(s1);
+            t1 = warp_sum(t1);
+            if (lane == k) { mS1 = s0; mA1 = t0; }
+            if (lane == k + 1) { mS1 = s1; mA1 = t1; }
+        }
+        if (have) {
             long long psi[15];
-            orbit_equations(e - b, a, sS1, sA1 / 2, psi);
+            orbit_equations(rx.z - rx.x, a, mS1, mA1 / 2, psi);
             if (induced) to_induced(psi);
-            long long v = psi[0];
+            long long *o = out + (size_t)px * 15;
 #pragma unroll
-            for (int k = 1; k < 15; ++k)
-                if (lane == k) v = psi[k];
-            out[(size_t)perm[x] * 15 + lane] = v;
+            for (int k = 0; k < 15; ++k) o[k] = psi[k];
         }
     }
 }
