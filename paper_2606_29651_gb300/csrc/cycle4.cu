@@ -118,6 +118,12 @@ __device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, in
     }
 }
 
+// First probe of key w in a table of mask + 1 = 2^k slots: the top k bits of
+// w times 2^32 / golden ratio (Fibonacci hashing), two instructions.
+__device__ __forceinline__ unsigned fib_slot(int w, unsigned mask) {
+    return (static_cast<unsigned>(w) * 0x9E3779B1u) >> (__clz(mask + 1) + 1);
+}
+
 // Split table: keys (-1 empty) and counts in two arrays.
 struct SplitTab {
     int *hk, *hc;
@@ -125,7 +131,7 @@ struct SplitTab {
     unsigned short *touched;   // slots filled (CTA groups)
     // counts w; returns the slot if this call inserted w, -1 if w was there
     __device__ __forceinline__ int add(int w) const {
-        unsigned s = hash_slot(w, mask);
+        unsigned s = fib_slot(w, mask);
         for (unsigned probe = 0; probe <= mask; ++probe) {
             const int prev = atomicCAS(&hk[s], -1, w);
             if (prev == -1) { atomicAdd(&hc[s], 1); return (int)s; }
@@ -134,7 +140,16 @@ struct SplitTab {
         }
         return -1;
     }
-    __device__ __forceinline__ int get(int w) const { return hcount_get(hk, hc, mask, w); }
+    __device__ __forceinline__ int get(int w) const {
+        unsigned s = fib_slot(w, mask);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            const int k = hk[s];
+            if (k == w) return hc[s];
+            if (k == -1) return 0;
+            s = (s + 1) & mask;
+        }
+        return 0;
+    }
     __device__ __forceinline__ bool empty(int s) const { return hk[s] == -1; }
     __device__ __forceinline__ int key(int s) const { return hk[s]; }
     __device__ __forceinline__ int cnt(int s) const { return hc[s]; }
@@ -154,7 +169,7 @@ struct PackedTab {
     unsigned short *touched;   // slots filled (CTA groups)
     __device__ __forceinline__ int add(int w) const {
         const unsigned key = static_cast<unsigned>(w);
-        unsigned s = hash_slot(w, mask);
+        unsigned s = fib_slot(w, mask);
         for (unsigned probe = 0; probe <= mask; ++probe) {
             const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
             if (prev == EMPTY) return (int)s;
@@ -165,7 +180,7 @@ struct PackedTab {
     }
     __device__ __forceinline__ int get(int w) const {
         const unsigned key = static_cast<unsigned>(w);
-        unsigned s = hash_slot(w, mask);
+        unsigned s = fib_slot(w, mask);
         for (unsigned probe = 0; probe <= mask; ++probe) {
             const unsigned cur = t[s];
             if (cur == EMPTY) return 0;
