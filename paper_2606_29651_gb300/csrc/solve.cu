@@ -76,19 +76,42 @@ __device__ __forceinline__ void to_induced(long long *p) {
     p[10] = i10; p[11] = i11; p[12] = i12; p[13] = i13; p[14] = i14;
 }
 
-// A warp takes 32 consecutive vertices: each lane loads its vertex's row
-// bounds, accumulators and output row up front; the warp then sums S1 and
-// A1 over the neighbours of each of the 32 vertices in turn (coalesced
-// gathers, two vertices in flight), and each lane solves and writes its own
-// vertex.
+// Vertices below `bound` (ids are in degree-class order, so these are the
+// rows shorter than the long-row class): a warp takes 32 consecutive
+// vertices, each lane loads its vertex's row bounds and accumulators up
+// front, the warp sums S1 and A1 over the neighbours of each of the 32 in
+// turn (coalesced gathers, two vertices in flight), and each lane solves and
+// writes its own vertex. Longer rows: one warp per vertex.
+__device__ __forceinline__ void solve_write(long long d, const VAcc &a, long long sS1, long long sA1, int induced,
+                                            long long *o) {
+    long long psi[15];
+    orbit_equations(d, a, sS1, sA1 / 2, psi);
+    if (induced) to_induced(psi);
+#pragma unroll
+    for (int k = 0; k < 15; ++k) o[k] = psi[k];
+}
+
 __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const int *perm, long long *out,
-                                               int induced) {
+                                               int induced, const int *coff, int ntiles, int long_class) {
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int x0 = gw * 32; x0 < g.n; x0 += nw * 32) {
+    const int bound = min(coff[long_class * ntiles], g.n);
+    for (int x = bound + gw; x < g.n; x += nw) {
+        const int4 rx = g.rinfo[x];
+        long long sS1 = 0, sA1 = 0;
+        for (int p = rx.x + lane; p < rx.z; p += 32) {
+            const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[p]]);
+            sS1 += sa.x;
+            sA1 += sa.y;
+        }
+        sS1 = warp_sum(sS1);
+        sA1 = warp_sum(sA1);
+        if (lane == 0) solve_write(rx.z - rx.x, vacc[x], sS1, sA1, induced, out + (size_t)perm[x] * 15);
+    }
+    for (int x0 = gw * 32; x0 < bound; x0 += nw * 32) {
         const int x = x0 + lane;
-        const bool have = x < g.n;
+        const bool have = x < bound;
         int4 rx = make_int4(0, 0, 0, 0);
         VAcc a{};
         int px = 0;
@@ -98,7 +121,7 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
             px = perm[x];
         }
         long long mS1 = 0, mA1 = 0;   // this lane's vertex
-        const int cnt = min(32, g.n - x0);
+        const int cnt = min(32, bound - x0);
         for (int k = 0; k < cnt; k += 2) {
             const int b0 = __shfl_sync(FULL, rx.x, k), e0 = __shfl_sync(FULL, rx.z, k);
             const int b1 = __shfl_sync(FULL, rx.x, k + 1 < 32 ? k + 1 : 31);
@@ -123,20 +146,14 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
             if (lane == k) { mS1 = s0; mA1 = t0; }
             if (lane == k + 1) { mS1 = s1; mA1 = t1; }
         }
-        if (have) {
-            long long psi[15];
-            orbit_equations(rx.z - rx.x, a, mS1, mA1 / 2, psi);
-            if (induced) to_induced(psi);
-            long long *o = out + (size_t)px * 15;
-#pragma unroll
-            for (int k = 0; k < 15; ++k) o[k] = psi[k];
-        }
+        if (have) solve_write(rx.z - rx.x, a, mS1, mA1, induced, out + (size_t)px * 15);
     }
 }
 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
-    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], 256, 0, st>>>(g, w.vacc, w.perm, out, w.induced);
+    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], 256, 0, st>>>(g, w.vacc, w.perm, out, w.induced, w.coff,
+                                                                  w.ntiles, w.tune[TUNE_LONG_ROW_CLASS]);
     after_launch(st, K_SOLVE);
 }
 
