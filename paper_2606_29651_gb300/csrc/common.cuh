@@ -204,14 +204,13 @@ __device__ __forceinline__ void seg_visit(const int *__restrict__ col, const Seg
 #pragma unroll
         for (int r = 0; r < U; ++r) {
             const int ws = w0 + r * stride;
-            q[r] = 0;
-            pos[r] = -1;
-            val[r] = 0;
-            if (ws >= total) continue;   // warp-uniform: windows past the end
             const bool starts = mylen > 0 && mypre >= ws && mypre < ws + 32;
             const unsigned sb = __reduce_or_sync(FULL, starts ? (1u << (mypre - ws)) : 0u);
             const int before = __popc(__ballot_sync(FULL, mylen > 0 && mypre < ws));
             const int k = ws + lane;
+            q[r] = 0;
+            pos[r] = -1;
+            val[r] = 0;
             if (k < total) {
                 const int rk = before + __popc(sb & le) - 1;
                 q[r] = T.idx[rk];
@@ -220,8 +219,7 @@ __device__ __forceinline__ void seg_visit(const int *__restrict__ col, const Seg
             }
         }
 #pragma unroll
-        for (int r = 0; r < U; ++r)
-            if (w0 + r * stride < total) f(pos[r] >= 0, q[r], pos[r], val[r]);
+        for (int r = 0; r < U; ++r) f(pos[r] >= 0, q[r], pos[r], val[r]);
     }
 }
 

@@ -204,8 +204,8 @@ struct PackedTab {
 // A repeated key is a 4-cycle, so roots without one skip the credit and
 // middle passes. A CTA records the slots it fills in `touched` (flags[0]
 // counts them, flags[1] notes a repeated key) and empties only those; a warp
-// keeps no list: its table is sized to the root (4W slots up to the whole
-// table), and it sweeps that region.
+// keeps no list: its table is sized to the root (at least twice W slots),
+// and it sweeps that region.
 // pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
 // the CTA).
 template <bool CTA, class Tab>
@@ -328,8 +328,8 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             }
             continue;
         }
-        // at least 4W slots (short probe runs), else the whole table (W <= 3/4 of it)
-        unsigned slots = next_pow2(4 * (unsigned)ub);
+        // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
+        unsigned slots = next_pow2(2 * (unsigned)ub);
         slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
         const PackedTab T{S.t, slots - 1, cb, nullptr};
         c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
