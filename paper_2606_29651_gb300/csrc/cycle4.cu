@@ -302,37 +302,66 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
     const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
     PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
     __syncwarp();
-    for (int u = gw; u < g.n; u += nw) {
-        const int4 ru = g.rinfo[u];
-        const int b = ru.x, din = ru.y - ru.x;
-        if (din < 2) continue;
-        long long ub = 0;   // exact wedge count W of root u
-        Chunk0 c0pre{false, 0, 0, 0, 0};
-        if (din <= 32) {   // one chunk: its segment table gives W
-            c0pre.total = wedge_chunk(g, u, b, din, 0, S.seg, c0pre.v, c0pre.len, c0pre.pre);
-            c0pre.built = true;
-            ub = c0pre.total;
-        } else {
-            for (int p = lane; p < din; p += 32) ub += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
-            ub = warp_sum(ub);
-        }
-        if (ub < 2) continue;
-        if (ub > maxub || ub > pack_lim) {
-            if (lane == 0) {
-                int which, list;   // queue counter and list slot (lists + list * n)
-                if (ub > CC_MAXUB) { which = CNT_C4_GLOBAL; list = 4; }
-                else if (ub <= 2 * CM_MAXUB && ub <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
-                else if (ub <= CM_MAXUB) { which = CNT_C4_MID; list = 2; }
-                else { which = CNT_C4_CTA; list = 3; }
-                lists[(size_t)list * g.n + atomicAdd(&counters[which], 1)] = u;
+    // Software pipeline over the warp's roots u, u + nw, u + 2 nw: row bounds
+    // are loaded two roots ahead, the first 32 in-neighbours and their row
+    // bounds one root ahead, so that a root starts with its data in flight.
+    const int4 Z = make_int4(0, 0, 0, 0);
+    int u = gw;
+    int4 ru = u < g.n ? g.rinfo[u] : Z;
+    int4 ru1 = u + nw < g.n ? g.rinfo[u + nw] : Z;
+    int v0 = (u < g.n && lane < ru.y - ru.x) ? g.ncol[ru.x + lane] : -1;
+    int4 rv0 = v0 >= 0 ? g.rinfo[v0] : Z;
+    for (; u < g.n; u += nw) {
+        const int u2 = u + 2 * nw;
+        const int4 ru2 = u2 < g.n ? g.rinfo[u2] : Z;
+        const int v1 = (u + nw < g.n && lane < ru1.y - ru1.x) ? g.ncol[ru1.x + lane] : -1;
+        int4 rv1 = Z;
+        bool rv1_loaded = false;
+        [&] {
+            const int b = ru.x, din = ru.y - ru.x;
+            if (din < 2) return;
+            long long ub = 0;   // exact wedge count W of root u
+            Chunk0 c0pre{false, 0, 0, 0, 0};
+            if (din <= 32) {   // one chunk: its segment table gives W
+                int st = 0, len = 0;
+                if (lane < din) {
+                    st = rv0.x;
+                    len = wedge_len(g, u, rv0);
+                }
+                c0pre.v = v0;
+                c0pre.len = len;
+                c0pre.total = seg_build(S.seg, st, len, c0pre.pre);
+                c0pre.built = true;
+                ub = c0pre.total;
+            } else {
+                for (int p = lane; p < din; p += 32) ub += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
+                ub = warp_sum(ub);
             }
-            continue;
-        }
-        // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
-        unsigned slots = next_pow2(2 * (unsigned)ub);
-        slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
-        const PackedTab T{S.t, slots - 1, cb, nullptr};
-        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
+            rv1 = v1 >= 0 ? g.rinfo[v1] : Z;   // next root's in-neighbours, during this walk
+            rv1_loaded = true;
+            if (ub < 2) return;
+            if (ub > maxub || ub > pack_lim) {
+                if (lane == 0) {
+                    int which, list;   // queue counter and list slot (lists + list * n)
+                    if (ub > CC_MAXUB) { which = CNT_C4_GLOBAL; list = 4; }
+                    else if (ub <= 2 * CM_MAXUB && ub <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
+                    else if (ub <= CM_MAXUB) { which = CNT_C4_MID; list = 2; }
+                    else { which = CNT_C4_CTA; list = 3; }
+                    lists[(size_t)list * g.n + atomicAdd(&counters[which], 1)] = u;
+                }
+                return;
+            }
+            // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
+            unsigned slots = next_pow2(2 * (unsigned)ub);
+            slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
+            const PackedTab T{S.t, slots - 1, cb, nullptr};
+            c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
+        }();
+        if (!rv1_loaded) rv1 = v1 >= 0 ? g.rinfo[v1] : Z;
+        ru = ru1;
+        ru1 = ru2;
+        v0 = v1;
+        rv0 = rv1;
     }
 }
 
