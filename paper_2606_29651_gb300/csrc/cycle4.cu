@@ -29,6 +29,7 @@ namespace niorca {
 constexpr int CW_WARPS = 4;
 constexpr int CW_SLOTS = 2048;      // packed
 constexpr int CW_MAXUB = 1536;
+constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
 constexpr int CM_THREADS = 128;
 constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
 constexpr int CM_MAXUB = 3072;      // split; 6144 when packed
@@ -178,6 +179,22 @@ struct PackedTab {
         }
         return -1;
     }
+    // add, also telling whether this call raised w's count from 1 to 2
+    __device__ __forceinline__ int add(int w, bool &became2) const {
+        const unsigned key = static_cast<unsigned>(w);
+        unsigned s = fib_slot(w, mask);
+        became2 = false;
+        for (unsigned probe = 0; probe <= mask; ++probe) {
+            const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
+            if (prev == EMPTY) return (int)s;
+            if ((prev >> cb) == key) {
+                became2 = (atomicAdd(&t[s], 1u) & ((1u << cb) - 1)) == 1;
+                return -1;
+            }
+            s = (s + 1) & mask;
+        }
+        return -1;
+    }
     __device__ __forceinline__ int get(int w) const {
         const unsigned key = static_cast<unsigned>(w);
         unsigned s = fib_slot(w, mask);
@@ -216,13 +233,19 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
     };
-    bool dup_l = false;   // warp group: this lane saw a repeated key
     auto insert = [&](bool act, int, int w) {
-        const int slot = act ? T.add(w) : -2;
-        if (!CTA) {
-            dup_l |= slot == -1;
+        if constexpr (!CTA) {
+            // a warp lists the keys that reach a count of 2: flags[0] of them
+            // in flags[1 ..] (CW_DUPS at most; more only raise the count)
+            bool became2 = false;
+            if (act) T.add(w, became2);
+            if (became2) {
+                const int i = atomicAdd(&flags[0], 1);
+                if (i < CW_DUPS) flags[1 + i] = w;
+            }
             return;
         }
+        const int slot = act ? T.add(w) : -2;
         // new keys of the warp take consecutive `touched` entries
         const unsigned fresh = __ballot_sync(FULL, slot >= 0);
         const unsigned dups = __ballot_sync(FULL, slot == -1);
@@ -239,7 +262,30 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {}, c0pre);
     sync();
     const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
-    if (CTA ? flags[1] != 0 : __any_sync(FULL, dup_l)) {
+    bool sweep = CTA ? flags[1] != 0 : false;
+    if (!CTA) {
+        const int nd = flags[0];
+        if (nd > CW_DUPS) {
+            sweep = true;
+        } else if (nd > 0) {
+            // few repeated keys: credit each directly; its middle vertices are
+            // N-(u) ∩ N(w), found by searching row w for each in-neighbour
+            long long su = 0;
+            for (int k = 0; k < nd; ++k) {
+                const int w = flags[1 + k];
+                const int c = T.get(w);
+                su += c2(c);
+                const int4 rw = g.rinfo[w];
+                for (int p = lane; p < din; p += 32) {
+                    const int v = g.ncol[b + p];
+                    if (find_sorted(g.ncol, rw.x, rw.z, v) >= 0) add64(&vacc[v].C4, c - 1);
+                }
+                if (lane == 0) add64(&vacc[w].C4, c2(c));
+            }
+            if (lane == 0) add64(&vacc[u].C4, su);
+        }
+    }
+    if (sweep) {
         long long su = 0;
         for (int i = tid; i < nt; i += nthreads) {
             const int slot = CTA ? T.touched[i] : i;
@@ -278,6 +324,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         }
     } else {
         T.clear_all(tid, nthreads);
+        if (lane == 0) flags[0] = 0;
     }
     sync();
 }
@@ -288,6 +335,7 @@ struct __align__(16) C4WarpSmem {
     unsigned t[CW_SLOTS];
     SegTab seg;
     long long pv[32];
+    int dups[1 + CW_DUPS];   // count, then keys that reached a count of 2
 };
 
 // One warp per root with W <= maxub (<= CW_MAXUB) that fits a packed table;
@@ -301,6 +349,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
     PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
+    if (lane == 0) S.dups[0] = 0;
     __syncwarp();
     // Software pipeline over the warp's roots u, u + nw, u + 2 nw: row bounds
     // are loaded two roots ahead, the first 32 in-neighbours and their row
@@ -355,7 +404,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             unsigned slots = next_pow2(2 * (unsigned)ub);
             slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
             const PackedTab T{S.t, slots - 1, cb, nullptr};
-            c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, nullptr, c0pre);
+            c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
         }();
         if (!rv1_loaded) rv1 = v1 >= 0 ? g.rinfo[v1] : Z;
         ru = ru1;
