@@ -179,22 +179,6 @@ struct PackedTab {
         }
         return -1;
     }
-    // add, also telling whether this call raised w's count from 1 to 2
-    __device__ __forceinline__ int add(int w, bool &became2) const {
-        const unsigned key = static_cast<unsigned>(w);
-        unsigned s = fib_slot(w, mask);
-        became2 = false;
-        for (unsigned probe = 0; probe <= mask; ++probe) {
-            const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
-            if (prev == EMPTY) return (int)s;
-            if ((prev >> cb) == key) {
-                became2 = (atomicAdd(&t[s], 1u) & ((1u << cb) - 1)) == 1;
-                return -1;
-            }
-            s = (s + 1) & mask;
-        }
-        return -1;
-    }
     __device__ __forceinline__ int get(int w) const {
         const unsigned key = static_cast<unsigned>(w);
         unsigned s = fib_slot(w, mask);
@@ -233,19 +217,13 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
     };
+    bool dup_l = false;   // warp group: this lane saw a repeated key
     auto insert = [&](bool act, int, int w) {
-        if constexpr (!CTA) {
-            // a warp lists the keys that reach a count of 2: flags[0] of them
-            // in flags[1 ..] (CW_DUPS at most; more only raise the count)
-            bool became2 = false;
-            if (act) T.add(w, became2);
-            if (became2) {
-                const int i = atomicAdd(&flags[0], 1);
-                if (i < CW_DUPS) flags[1 + i] = w;
-            }
+        const int slot = act ? T.add(w) : -2;
+        if (!CTA) {
+            dup_l |= slot == -1;
             return;
         }
-        const int slot = act ? T.add(w) : -2;
         // new keys of the warp take consecutive `touched` entries
         const unsigned fresh = __ballot_sync(FULL, slot >= 0);
         const unsigned dups = __ballot_sync(FULL, slot == -1);
@@ -263,31 +241,48 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     sync();
     const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
     bool sweep = CTA ? flags[1] != 0 : false;
-    if (!CTA) {
-        const int nd = flags[0];
-        if (nd > CW_DUPS) {
-            sweep = true;
-        } else if (nd > 0) {
-            // few repeated keys: credit each directly; its middle vertices are
-            // N-(u) ∩ N(w), found by searching row w for each in-neighbour
-            long long su = 0;
-            for (int k = 0; k < nd; ++k) {
-                const int w = flags[1 + k];
-                const int c = T.get(w);
+    if (!CTA && __any_sync(FULL, dup_l)) {
+        // A warp sweeps its table for the repeated keys (count >= 2), credits
+        // them, and lists up to CW_DUPS of them in flags[]; the middle
+        // vertices of key w are N-(u) ∩ N(w), found by searching row w for
+        // each in-neighbour. More repeated keys: the middle walk below.
+        long long su = 0;
+        int nd = 0;
+        for (int i = lane; i < nt; i += 32) {
+            const int c = T.empty(i) ? 0 : T.cnt(i);
+            const unsigned rep = __ballot_sync(FULL, c >= 2);   // nt is a multiple of 32
+            if (c >= 2) {
+                const int w = T.key(i);
                 su += c2(c);
+                add64(&vacc[w].C4, c2(c));
+                const int k = nd + __popc(rep & lanemask_lt());
+                if (k < CW_DUPS) {
+                    flags[k] = w;
+                    flags[CW_DUPS + k] = c;
+                }
+            }
+            nd += __popc(rep);
+        }
+        su = warp_sum(su);
+        if (lane == 0) add64(&vacc[u].C4, su);
+        __syncwarp();
+        if (nd <= CW_DUPS) {
+            for (int k = 0; k < nd; ++k) {
+                const int w = flags[k], c = flags[CW_DUPS + k];
                 const int4 rw = g.rinfo[w];
                 for (int p = lane; p < din; p += 32) {
                     const int v = g.ncol[b + p];
                     if (find_sorted(g.ncol, rw.x, rw.z, v) >= 0) add64(&vacc[v].C4, c - 1);
                 }
-                if (lane == 0) add64(&vacc[w].C4, c2(c));
             }
-            if (lane == 0) add64(&vacc[u].C4, su);
+            __syncwarp();
+        } else {
+            sweep = true;   // credits done; middle walk only
         }
     }
     if (sweep) {
         long long su = 0;
-        for (int i = tid; i < nt; i += nthreads) {
+        for (int i = tid; i < (CTA ? nt : 0); i += nthreads) {
             const int slot = CTA ? T.touched[i] : i;
             if (!CTA && T.empty(slot)) continue;
             const int c = T.cnt(slot);
@@ -297,7 +292,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
             }
         }
         su = warp_sum(su);
-        if (lane == 0 && su) add64(&vacc[u].C4, su);
+        if (CTA && lane == 0 && su) add64(&vacc[u].C4, su);
         // middle vertices: each wedge through v adds c_w - 1
         if (tid < 32) pv[tid] = 0;
         sync();
@@ -324,7 +319,6 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         }
     } else {
         T.clear_all(tid, nthreads);
-        if (lane == 0) flags[0] = 0;
     }
     sync();
 }
@@ -335,7 +329,7 @@ struct __align__(16) C4WarpSmem {
     unsigned t[CW_SLOTS];
     SegTab seg;
     long long pv[32];
-    int dups[1 + CW_DUPS];   // count, then keys that reached a count of 2
+    int dups[2 * CW_DUPS];   // repeated keys of a root and their counts
 };
 
 // One warp per root with W <= maxub (<= CW_MAXUB) that fits a packed table;
@@ -349,7 +343,6 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
     PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
-    if (lane == 0) S.dups[0] = 0;
     __syncwarp();
     // Software pipeline over the warp's roots u, u + nw, u + 2 nw: row bounds
     // are loaded two roots ahead, the first 32 in-neighbours and their row
