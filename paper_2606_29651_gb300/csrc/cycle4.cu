@@ -296,10 +296,9 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         // middle vertices: each wedge through v adds c_w - 1
         if (tid < 32) pv[tid] = 0;
         sync();
-        auto middle = [&](bool act, int q, int w) {
-            if (!act) return;
-            const int c = T.get(w);
-            if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
+        auto middle = [&](bool act, int q, int w) {   // lanes of one v add once
+            const int c = act ? T.get(w) : 0;
+            warp_add_ll(c > 1, &pv[q], q, c - 1);
         };
         auto flush = [&](int v) {
             const long long x = pv[lane];
@@ -571,14 +570,16 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
         __syncwarp();
         pass(
             [&](bool act, int q, int w) {
-                if (!act) return;
-                const int old = atomicOr(&row[w], (int)0x80000000);
-                const int c = old & 0x7fffffff;
-                if (c > 1) atomicAdd((unsigned long long *)&pv[q], (unsigned long long)(c - 1));
-                if (old >= 0 && c >= 2) {   // first visitor of this key
-                    su += c2(c);
-                    add64(&vacc[w].C4, c2(c));
+                int c = 0;
+                if (act) {
+                    const int old = atomicOr(&row[w], (int)0x80000000);
+                    c = old & 0x7fffffff;
+                    if (old >= 0 && c >= 2) {   // first visitor of this key
+                        su += c2(c);
+                        add64(&vacc[w].C4, c2(c));
+                    }
                 }
+                warp_add_ll(c > 1, &pv[q], q, c - 1);   // lanes of one v add once
             },
             [&](int v) {
                 const long long x = pv[lane];
