@@ -298,7 +298,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         sync();
         auto middle = [&](bool act, int q, int w) {   // lanes of one v add once
             const int c = act ? T.get(w) : 0;
-            warp_add_ll(c > 1, &pv[q], q, c - 1);
+            if (__any_sync(FULL, c > 1)) warp_add_ll(c > 1, &pv[q], q, c - 1);
         };
         auto flush = [&](int v) {
             const long long x = pv[lane];
@@ -579,7 +579,7 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
                         add64(&vacc[w].C4, c2(c));
                     }
                 }
-                warp_add_ll(c > 1, &pv[q], q, c - 1);   // lanes of one v add once
+                if (__any_sync(FULL, c > 1)) warp_add_ll(c > 1, &pv[q], q, c - 1);   // lanes of one v add once
             },
             [&](int v) {
                 const long long x = pv[lane];
