@@ -44,6 +44,16 @@ constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
+// Adds c - 1 to pv[q] for the lanes with c > 1: one warp-aggregated atomic
+// per in-neighbour when many lanes take part (long rows of hub roots), plain
+// shared atomics when few do.
+__device__ __forceinline__ void add_middle(long long *pv, int q, int c) {
+    const unsigned m = __ballot_sync(FULL, c > 1);
+    if (!m) return;
+    if (__popc(m) > 8) warp_add_ll(c > 1, &pv[q], q, c - 1);
+    else if (c > 1) atomicAdd(reinterpret_cast<unsigned long long *>(&pv[q]), (unsigned long long)(c - 1));
+}
+
 // Wedges u - v - w through the in-neighbour v of root u: the entries of row
 // v below u, i.e. the position of u in row v (u is in N+(v)), found by a
 // search of N+(v) whose last steps touch the lines the walk reads next.
@@ -298,7 +308,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         sync();
         auto middle = [&](bool act, int q, int w) {   // lanes of one v add once
             const int c = act ? T.get(w) : 0;
-            if (__any_sync(FULL, c > 1)) warp_add_ll(c > 1, &pv[q], q, c - 1);
+            add_middle(pv, q, c);
         };
         auto flush = [&](int v) {
             const long long x = pv[lane];
@@ -579,7 +589,7 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
                         add64(&vacc[w].C4, c2(c));
                     }
                 }
-                if (__any_sync(FULL, c > 1)) warp_add_ll(c > 1, &pv[q], q, c - 1);   // lanes of one v add once
+                add_middle(pv, q, c);   // lanes of one v add once
             },
             [&](int v) {
                 const long long x = pv[lane];
