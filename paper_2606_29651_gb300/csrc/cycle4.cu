@@ -573,12 +573,33 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
                 __syncwarp();
             }
         };
+        // Roots with many wedges for their row (W > u / 16) read the counts
+        // back in a coalesced sweep of row[0, u) for the C(c, 2) credits and
+        // with plain loads for the middle sums, and clear the row with a
+        // coalesced sweep; others mark first visitors and clear per wedge.
+        const bool sweep = (long long)W * 16 > u;
+        const int gt = (int)cluster.block_rank() * CT_THREADS + threadIdx.x;
+        constexpr int GT = CT_CLUSTER * CT_THREADS;
         pass([&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); }, [](int) {});
         cluster.sync();
         long long su = 0;
         pv[lane] = 0;
         __syncwarp();
-        pass(
+        auto flush = [&](int v) {
+            const long long x = pv[lane];
+            if (x) add64(&vacc[v].C4, x);
+            pv[lane] = 0;
+        };
+        if (sweep) {
+            for (int w = gt; w < u; w += GT) {
+                const int c = row[w];
+                if (c >= 2) {
+                    su += c2(c);
+                    add64(&vacc[w].C4, c2(c));
+                }
+            }
+            pass([&](bool act, int q, int w) { add_middle(pv, q, act ? row[w] : 0); }, flush);
+        } else pass(
             [&](bool act, int q, int w) {
                 int c = 0;
                 if (act) {
@@ -591,15 +612,15 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
                 }
                 add_middle(pv, q, c);   // lanes of one v add once
             },
-            [&](int v) {
-                const long long x = pv[lane];
-                if (x) add64(&vacc[v].C4, x);
-                pv[lane] = 0;
-            });
+            flush);
         su = warp_sum(su);
         if (lane == 0 && su) add64(&vacc[u].C4, su);
         cluster.sync();
-        pass([&](bool act, int, int w) { if (act) row[w] = 0; }, [](int) {});
+        if (sweep) {
+            for (int w = gt; w < u; w += GT) row[w] = 0;
+        } else {
+            pass([&](bool act, int, int w) { if (act) row[w] = 0; }, [](int) {});
+        }
         cluster.sync();
     }
 }
