@@ -290,28 +290,44 @@ def run_ours(args) -> None:
     top_name, (top_ms, top_calls) = max(prof.items(), key=lambda kv: kv[1][0])
     top_avg_ms = top_ms / top_calls
 
-    # end to end through the public call, graph in pinned host memory
+    # End to end through the public call with the graph and the counts in
+    # pinned host memory: niorca_count_host reads the CSR and writes the
+    # counts across the host link inside the timed region (no staging copy;
+    # the transfers overlap the kernels). The staged variant (copy in, count,
+    # copy out on one stream) is timed as well.
     h_rp = torch.from_numpy(rp).pin_memory()
     h_ci = torch.from_numpy(ci).pin_memory()
     h_out = torch.empty((n, 15), dtype=torch.int64).pin_memory()
-    e_rp = torch.empty_like(d_rp)
-    e_ci = torch.empty_like(d_ci)
     e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i)
+        e_s[i].record(stream)
+        ni.count_host(h_rp, h_ci, h_out)
+        e_e[i].record(stream)
+    torch.cuda.synchronize(dev)
+    ni.check()
+    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
+    if not torch.equal(h_out, out.cpu()):
+        raise RuntimeError("end-to-end output differs from the resident-input output")
+    h_out2 = torch.empty((n, 15), dtype=torch.int64).pin_memory()
+    e_rp = torch.empty_like(d_rp)
+    e_ci = torch.empty_like(d_ci)
     for i in range(args.steps):
         flush.fill_(i)
         e_s[i].record(stream)
         e_rp.copy_(h_rp, non_blocking=True)
         e_ci.copy_(h_ci, non_blocking=True)
         ni.count(e_rp, e_ci, out)
-        h_out.copy_(out, non_blocking=True)
+        h_out2.copy_(out, non_blocking=True)
         e_e[i].record(stream)
     torch.cuda.synchronize(dev)
     ni.check()
-    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
+    staged_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
     e2e_ms = reduce_max(e2e_ms, world, dev)
-    if not torch.equal(h_out, out.cpu()):
-        raise RuntimeError("end-to-end output differs from the resident-input output")
+    staged_ms = reduce_max(staged_ms, world, dev)
+    if not torch.equal(h_out2, h_out):
+        raise RuntimeError("staged end-to-end output differs")
 
     if rank != 0:
         if world > 1:
@@ -344,7 +360,11 @@ def run_ours(args) -> None:
                    "l2": "flushed between timed steps (512 MB write); working set 0.6 GB",
                    "parallelism": "replicas" if world > 1 else "single"},
         "e2e": {"value": world * edges / (e2e_ms * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes), "d2h_bytes_per_step": int(n * 15 * 8)},
+                "h2d_bytes_per_step": int(rp.nbytes + ci.nbytes), "d2h_bytes_per_step": int(n * 15 * 8),
+                "call": "niorca_count_host on pinned host CSR and output (read and written across the host link "
+                        "inside the call)",
+                "staged_value": world * edges / (staged_ms * 1e-3),
+                "staged_call": "copy CSR in, niorca_count, copy counts out, one stream"},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
         "roofline": roofline,

@@ -72,6 +72,27 @@ niorca_status niorca_count(const int32_t *rowptr, const int32_t *colidx, int32_t
                            int64_t *out, void *stream);
 
 /*
+ * Orbit counts of one graph whose CSR and output live in HOST memory, with
+ * no staging copy: the kernels that read the CSR (the degree-class pass and
+ * the row relabelling, each reading it once in order) load it across the
+ * host link, and the orbit solve stores the counts into `out` in blocks of
+ * 32 contiguous rows. On GB300 (Grace host, NVLink-C2C) the transfers thus
+ * overlap the kernels instead of preceding and following them.
+ *   rowptr  host int32[n + 1], colidx host int32[m], out host int64[n * 15],
+ *           same meaning and layout as niorca_count; each must be
+ *           page-locked (cudaHostAlloc / cudaHostRegister) or reachable by
+ *           the device through coherent access to pageable memory. The
+ *           caller keeps them alive and unmodified until the stream reaches
+ *           the end of the call; `out` is complete only then.
+ *   stream  cudaStream_t to enqueue on
+ * Device pointers are accepted too. Returns NIORCA_EINVAL for a buffer the
+ * device cannot reach, otherwise as niorca_count. The paper has no
+ * counterpart: it concerns how the input reaches the GPU, not the method.
+ */
+niorca_status niorca_count_host(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                                int64_t *out, void *stream);
+
+/*
  * INDUCED orbit counts psi'_k(v) of one graph: the graphlet must be the
  * subgraph induced by its vertices (Def. 2), the variant ORCA counts and
  * that Sec. 5 contrasts with NI-ORCA (psi'13, psi'11, psi'10 are printed

@@ -46,6 +46,8 @@ def _lib():
     h.niorca_count.argtypes = [vp, vp, i32, i64, vp, vp]
     h.niorca_count_induced.restype = ctypes.c_int
     h.niorca_count_induced.argtypes = [vp, vp, i32, i64, vp, vp]
+    h.niorca_count_host.argtypes = [vp, vp, i32, i64, vp, vp]
+    h.niorca_count_host.restype = ctypes.c_int
     h.niorca_count_batch.restype = ctypes.c_int
     h.niorca_count_batch.argtypes = [vp, vp, vp, vp, i32, i64, i64, vp, vp]
     h.niorca_validate.restype = ctypes.c_int
@@ -120,6 +122,39 @@ def count(rowptr: torch.Tensor, colidx: torch.Tensor, out: torch.Tensor | None =
     st = _lib().niorca_count(_ptr(rowptr), _ptr(colidx), n, colidx.numel(), _ptr(out), _stream_ptr(stream))
     if st:
         raise NiorcaError(st, "niorca_count")
+    return out
+
+
+def _pinned(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if t.is_cuda or not t.is_pinned():
+        raise ValueError(f"{name} must be a pinned (page-locked) CPU tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def count_host(rowptr: torch.Tensor, colidx: torch.Tensor, out: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """psi[v, k] for a CSR graph in pinned host memory, written into pinned
+    host memory (niorca_count_host: the kernels read the CSR and write the
+    counts across the host link, with no staging copy).
+
+    Enqueues on `stream` (default: torch's current stream); `out` is valid
+    once the stream has reached the end of the call.
+    """
+    _pinned(rowptr, torch.int32, "rowptr")
+    _pinned(colidx, torch.int32, "colidx")
+    n = rowptr.numel() - 1
+    if out is None:
+        out = torch.empty((max(n, 0), 15), dtype=torch.int64).pin_memory()
+    _pinned(out, torch.int64, "out")
+    if out.numel() != 15 * max(n, 0):
+        raise ValueError("out must hold n * 15 int64")
+    st = _lib().niorca_count_host(_ptr(rowptr), _ptr(colidx), n, colidx.numel(), _ptr(out), _stream_ptr(stream))
+    if st:
+        raise NiorcaError(st, "niorca_count_host")
     return out
 
 

@@ -247,6 +247,38 @@ extern "C" niorca_status niorca_count(const int32_t *rowptr, const int32_t *coli
                nullptr, nullptr, 0);
 }
 
+namespace {
+// Whether the current device can load and store at `p` for `bytes` bytes
+// from kernels: page-locked host memory (or managed/device memory), or any
+// host memory where the device accesses pageable memory coherently.
+bool device_reachable(const void *p, size_t bytes) {
+    if (bytes == 0) return true;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
+        return true;
+    int dev = 0, pageable = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, dev) != cudaSuccess) return false;
+    return pageable != 0;
+}
+}  // namespace
+
+extern "C" niorca_status niorca_count_host(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
+                                           int64_t *out, void *stream) {
+    if (n < 0 || m < 0 || m > INT32_MAX) return NIORCA_EINVAL;
+    if (n == 0) return m == 0 ? NIORCA_OK : NIORCA_EINVAL;
+    if (!rowptr || !out || (m > 0 && !colidx)) return NIORCA_EINVAL;
+    if (!device_reachable(rowptr, 4 * ((size_t)n + 1)) || !device_reachable(colidx, 4 * (size_t)m) ||
+        !device_reachable(out, 120 * (size_t)n))
+        return NIORCA_EINVAL;
+    return run(rowptr, colidx, n, (int)m, reinterpret_cast<long long *>(out), static_cast<cudaStream_t>(stream),
+               nullptr, nullptr, 0);
+}
+
 extern "C" niorca_status niorca_count_induced(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m,
                                               int64_t *out, void *stream) {
     if (n < 0 || m < 0 || m > INT32_MAX) return NIORCA_EINVAL;

@@ -76,12 +76,14 @@ __device__ __forceinline__ void to_induced(long long *p) {
     p[10] = i10; p[11] = i11; p[12] = i12; p[13] = i13; p[14] = i14;
 }
 
-// Vertices below `bound` (ids are in degree-class order, so these are the
-// rows shorter than the long-row class): a warp takes 32 consecutive
-// vertices, each lane loads its vertex's row bounds and accumulators up
-// front, the warp sums S1 and A1 over the neighbours of each of the 32 in
-// turn (coalesced gathers, two vertices in flight), and each lane solves and
-// writes its own vertex. Longer rows: one warp per vertex.
+// Rows from the long-row class on (new ids from `bound`, the degree-class
+// order puts them last): one warp per vertex. Every other vertex is solved in
+// groups of 32 consecutive caller ids: each lane loads its vertex's row bounds
+// and accumulators up front, the warp sums S1 and A1 over the neighbours of
+// each of the 32 in turn (coalesced gathers, two vertices in flight), each
+// lane solves its own vertex, and the warp writes the group's 32 output rows
+// (3840 contiguous bytes) with coalesced stores through shared memory, which
+// also suits an output buffer in host memory.
 __device__ __forceinline__ void solve_write(long long d, const VAcc &a, long long sS1, long long sA1, int induced,
                                             long long *o) {
     long long psi[15];
@@ -91,9 +93,14 @@ __device__ __forceinline__ void solve_write(long long d, const VAcc &a, long lon
     for (int k = 0; k < 15; ++k) o[k] = psi[k];
 }
 
-__global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const int *perm, long long *out,
-                                               int induced, const int *coff, int ntiles, int long_class) {
+constexpr int SOLVE_WARPS = 8;
+
+__global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(Graph g, const VAcc *vacc, const int *perm,
+                                                            const int2 *vinfo, long long *out, int induced,
+                                                            const int *coff, int ntiles, int long_class) {
+    __shared__ long long obuf[SOLVE_WARPS][32 * 15];
     const int lane = lane_id();
+    long long *ob = obuf[threadIdx.x >> 5];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const int bound = min(coff[long_class * ntiles], g.n);
@@ -109,19 +116,23 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
         sA1 = warp_sum(sA1);
         if (lane == 0) solve_write(rx.z - rx.x, vacc[x], sS1, sA1, induced, out + (size_t)perm[x] * 15);
     }
-    for (int x0 = gw * 32; x0 < bound; x0 += nw * 32) {
-        const int x = x0 + lane;
-        const bool have = x < bound;
+    for (int xo0 = gw * 32; xo0 < g.n; xo0 += nw * 32) {
+        const int xo = xo0 + lane;   // caller id
+        int x = -1;                  // relabelled id, if this group solves it
+        if (xo < g.n) {
+            const int2 vi = vinfo[xo];
+            if (deg_class(vi.y) < long_class) x = vi.x;
+        }
+        const bool have = x >= 0;
+        const unsigned mine = __ballot_sync(FULL, have);
         int4 rx = make_int4(0, 0, 0, 0);
         VAcc a{};
-        int px = 0;
         if (have) {
             rx = g.rinfo[x];
             a = vacc[x];
-            px = perm[x];
         }
         long long mS1 = 0, mA1 = 0;   // this lane's vertex
-        const int cnt = min(32, bound - x0);
+        const int cnt = min(32, g.n - xo0);
         for (int k = 0; k < cnt; k += 2) {
             const int b0 = __shfl_sync(FULL, rx.x, k), e0 = __shfl_sync(FULL, rx.z, k);
             const int b1 = __shfl_sync(FULL, rx.x, k + 1 < 32 ? k + 1 : 31);
@@ -146,14 +157,19 @@ __global__ void __launch_bounds__(256) k_solve(Graph g, const VAcc *vacc, const 
             if (lane == k) { mS1 = s0; mA1 = t0; }
             if (lane == k + 1) { mS1 = s1; mA1 = t1; }
         }
-        if (have) solve_write(rx.z - rx.x, a, mS1, mA1, induced, out + (size_t)px * 15);
+        if (have) solve_write(rx.z - rx.x, a, mS1, mA1, induced, ob + lane * 15);
+        __syncwarp();
+        long long *o = out + (size_t)xo0 * 15;
+        for (int i = lane; i < cnt * 15; i += 32)
+            if ((mine >> (i / 15)) & 1u) o[i] = ob[i];
+        __syncwarp();
     }
 }
 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
-    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], 256, 0, st>>>(g, w.vacc, w.perm, out, w.induced, w.coff,
-                                                                  w.ntiles, w.tune[TUNE_LONG_ROW_CLASS]);
+    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], SOLVE_WARPS * 32, 0, st>>>(
+        g, w.vacc, w.perm, w.vinfo, out, w.induced, w.coff, w.ntiles, w.tune[TUNE_LONG_ROW_CLASS]);
     after_launch(st, K_SOLVE);
 }
 

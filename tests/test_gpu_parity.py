@@ -68,6 +68,30 @@ def test_complete_graphs_across_triangle_tiers(ni):
         assert_same(gpu_count(ni, *gg.complete(n)), np.tile(np.array(closed_complete(n)), (n, 1)), f"K{n}")
 
 
+@pytest.mark.parametrize("name,make", [
+    ("er2000", lambda: gg.er(2000, 0.01, 1)),
+    ("rmat12", lambda: gg.rmat(12, 16, seed=3)),
+    ("star3000", lambda: gg.star(3000)),          # a row of the long-row class
+    ("k300", lambda: gg.complete(300)),
+])
+def test_host_buffers_equal_device_buffers(ni, name, make):
+    # niorca_count_host reads the pinned CSR and writes the pinned counts in place
+    rp, ci = make()
+    h_rp = torch.from_numpy(np.ascontiguousarray(rp, np.int32)).pin_memory()
+    h_ci = torch.from_numpy(np.ascontiguousarray(ci, np.int32)).pin_memory()
+    got = ni.count_host(h_rp, h_ci)
+    torch.cuda.synchronize()
+    ni.check()
+    assert_same(got.numpy(), gpu_count(ni, rp, ci), name)
+    assert_same(got.numpy(), oracle.count(rp, ci), name + " vs oracle")
+
+
+def test_host_entry_rejects_unpinned_tensors(ni):
+    rp, ci = gg.er(100, 0.1, 2)
+    with pytest.raises(ValueError):
+        ni.count_host(torch.from_numpy(rp), torch.from_numpy(ci))
+
+
 def test_empty_and_edgeless(ni):
     rp = np.zeros(6, np.int32)
     assert_same(gpu_count(ni, rp, np.zeros(0, np.int32)), np.zeros((5, 15), np.int64), "edgeless")
