@@ -135,6 +135,13 @@ __device__ __forceinline__ unsigned fib_slot(int w, unsigned mask) {
     return (static_cast<unsigned>(w) * 0x9E3779B1u) >> (__clz(mask + 1) + 1);
 }
 
+// Second probe of a packed table: another multiplicative hash, so that keys
+// whose first slots collide part ways (shorter runs than linear probing from
+// the first slot); probing is linear from there.
+__device__ __forceinline__ unsigned fib_slot2(int w, unsigned mask) {
+    return (static_cast<unsigned>(w) * 0x85EBCA77u) >> (__clz(mask + 1) + 1);
+}
+
 // Split table: keys (-1 empty) and counts in two arrays.
 struct SplitTab {
     int *hk, *hc;
@@ -170,7 +177,8 @@ struct SplitTab {
     }
 };
 
-// Packed table: one word (w << cb) | count per slot, EMPTY when free. A
+// Packed table: one word (w << cb) | count per slot, EMPTY when free; the
+// probe sequence is fib_slot, fib_slot2, fib_slot2 + 1, ... A
 // count never reaches 2^cb - 1 (the caller ensures W < 2^cb - 1), so a full
 // word is never EMPTY.
 struct PackedTab {
@@ -185,7 +193,7 @@ struct PackedTab {
             const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
             if (prev == EMPTY) return (int)s;
             if ((prev >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
-            s = (s + 1) & mask;
+            s = probe == 0 ? fib_slot2(w, mask) : (s + 1) & mask;
         }
         return -1;
     }
@@ -196,7 +204,7 @@ struct PackedTab {
             const unsigned cur = t[s];
             if (cur == EMPTY) return 0;
             if ((cur >> cb) == key) return (int)(cur & ((1u << cb) - 1));
-            s = (s + 1) & mask;
+            s = probe == 0 ? fib_slot2(w, mask) : (s + 1) & mask;
         }
         return 0;
     }
