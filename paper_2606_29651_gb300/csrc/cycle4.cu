@@ -129,19 +129,6 @@ __device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, in
     }
 }
 
-// First probe of key w in a table of mask + 1 = 2^k slots: the top k bits of
-// w times 2^32 / golden ratio (Fibonacci hashing), two instructions.
-__device__ __forceinline__ unsigned fib_slot(int w, unsigned mask) {
-    return (static_cast<unsigned>(w) * 0x9E3779B1u) >> (__clz(mask + 1) + 1);
-}
-
-// Second probe of a packed table: another multiplicative hash, so that keys
-// whose first slots collide part ways (shorter runs than linear probing from
-// the first slot); probing is linear from there.
-__device__ __forceinline__ unsigned fib_slot2(int w, unsigned mask) {
-    return (static_cast<unsigned>(w) * 0x85EBCA77u) >> (__clz(mask + 1) + 1);
-}
-
 // Split table: keys (-1 empty) and counts in two arrays.
 struct SplitTab {
     int *hk, *hc;
@@ -154,7 +141,7 @@ struct SplitTab {
             const int prev = atomicCAS(&hk[s], -1, w);
             if (prev == -1) { atomicAdd(&hc[s], 1); return (int)s; }
             if (prev == w) { atomicAdd(&hc[s], 1); return -1; }
-            s = (s + 1) & mask;
+            s = next_probe(s, probe, w, mask);
         }
         return -1;
     }
@@ -164,7 +151,7 @@ struct SplitTab {
             const int k = hk[s];
             if (k == w) return hc[s];
             if (k == -1) return 0;
-            s = (s + 1) & mask;
+            s = next_probe(s, probe, w, mask);
         }
         return 0;
     }
@@ -177,8 +164,7 @@ struct SplitTab {
     }
 };
 
-// Packed table: one word (w << cb) | count per slot, EMPTY when free; the
-// probe sequence is fib_slot, fib_slot2, fib_slot2 + 1, ... A
+// Packed table: one word (w << cb) | count per slot, EMPTY when free. A
 // count never reaches 2^cb - 1 (the caller ensures W < 2^cb - 1), so a full
 // word is never EMPTY.
 struct PackedTab {
@@ -193,7 +179,7 @@ struct PackedTab {
             const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
             if (prev == EMPTY) return (int)s;
             if ((prev >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
-            s = probe == 0 ? fib_slot2(w, mask) : (s + 1) & mask;
+            s = next_probe(s, probe, w, mask);
         }
         return -1;
     }
@@ -204,7 +190,7 @@ struct PackedTab {
             const unsigned cur = t[s];
             if (cur == EMPTY) return 0;
             if ((cur >> cb) == key) return (int)(cur & ((1u << cb) - 1));
-            s = probe == 0 ? fib_slot2(w, mask) : (s + 1) & mask;
+            s = next_probe(s, probe, w, mask);
         }
         return 0;
     }
