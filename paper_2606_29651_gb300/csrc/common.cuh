@@ -81,44 +81,36 @@ __device__ __forceinline__ void add64(long long *p, long long v) {
 
 __device__ __forceinline__ void set_status(int *status, int bits) { atomicOr(status, bits); }
 
-// Probe sequence of the open-addressing tables keyed by vertex id, in a
-// power-of-two table of mask + 1 = 2^k slots: first the top k bits of the
-// key times 2^32 / golden ratio (Fibonacci hashing, two instructions), then
-// the top bits of a second multiplicative hash, then linear from there.
-// Keys whose first slots collide part ways at the second probe, which keeps
-// the runs (and a warp's slowest lane) short.
-__device__ __forceinline__ unsigned fib_slot(int key, unsigned mask) {
-    return (static_cast<unsigned>(key) * 0x9E3779B1u) >> (__clz(mask + 1) + 1);
-}
-__device__ __forceinline__ unsigned fib_slot2(int key, unsigned mask) {
-    return (static_cast<unsigned>(key) * 0x85EBCA77u) >> (__clz(mask + 1) + 1);
-}
-__device__ __forceinline__ unsigned next_probe(unsigned s, unsigned probe, int key, unsigned mask) {
-    return probe == 0 ? fib_slot2(key, mask) : (s + 1) & mask;
+// Multiplicative hash of a vertex id into a power-of-two table (the sets of
+// N+(u) in the triangle and aggregate stages, probed linearly: most probes
+// there are misses that end at the first slot).
+__device__ __forceinline__ unsigned hash_slot(int key, unsigned mask) {
+    unsigned h = static_cast<unsigned>(key) * 0x9E3779B1u;
+    return (h ^ (h >> 16)) & mask;
 }
 
 // Open-addressing set of vertex ids with a value (an index) per key.
-// Keys are -1 when empty. Capacity is a power of two (at least 2), at least
-// twice the number of keys inserted, so probes always end.
+// Keys are -1 when empty. Capacity is a power of two, at least twice the
+// number of keys inserted, so probes always end.
 __device__ __forceinline__ void hset_insert(int *keys, int *vals, unsigned mask, int key, int val) {
-    unsigned s = fib_slot(key, mask);
+    unsigned s = hash_slot(key, mask);
     for (unsigned probe = 0; probe <= mask; ++probe) {
         int prev = atomicCAS(&keys[s], -1, key);
         if (prev == -1 || prev == key) {
             vals[s] = val;
             return;
         }
-        s = next_probe(s, probe, key, mask);
+        s = (s + 1) & mask;
     }
 }
 
 __device__ __forceinline__ int hset_find(const int *keys, const int *vals, unsigned mask, int key) {
-    unsigned s = fib_slot(key, mask);
+    unsigned s = hash_slot(key, mask);
     for (unsigned probe = 0; probe <= mask; ++probe) {
         int k = keys[s];
         if (k == key) return vals[s];
         if (k == -1) return -1;
-        s = next_probe(s, probe, key, mask);
+        s = (s + 1) & mask;
     }
     return -1;
 }

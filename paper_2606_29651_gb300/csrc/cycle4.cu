@@ -129,6 +129,18 @@ __device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, in
     }
 }
 
+// Probe sequence of the 4-cycle count tables (mask + 1 = 2^k slots): first
+// the top k bits of the key times 2^32 / golden ratio (Fibonacci hashing),
+// then the top bits of a second multiplicative hash, then linear from there.
+// Keys whose first slots collide part ways at the second probe, which keeps
+// the runs, and so a warp's slowest insert, short.
+__device__ __forceinline__ unsigned fib_slot(int key, unsigned mask) {
+    return (static_cast<unsigned>(key) * 0x9E3779B1u) >> (__clz(mask + 1) + 1);
+}
+__device__ __forceinline__ unsigned next_probe(unsigned s, unsigned probe, int key, unsigned mask) {
+    return probe == 0 ? (static_cast<unsigned>(key) * 0x85EBCA77u) >> (__clz(mask + 1) + 1) : (s + 1) & mask;
+}
+
 // Split table: keys (-1 empty) and counts in two arrays.
 struct SplitTab {
     int *hk, *hc;
