@@ -30,8 +30,8 @@ constexpr int TS_MAXD = 256;  // out-degree handled by a 256-thread CTA (k_tri_c
 constexpr int TW_WARPS = 8;
 
 struct TriWarpSmem {
-    int hk[2 * TW_MAXD];
-    int hv[2 * TW_MAXD];
+    int hk[4 * TW_MAXD];   // N+(u) hash at load <= 1/4 (most probes are misses)
+    int hv[4 * TW_MAXD];
     int cnt[TW_MAXD];
     int kc[TW_MAXD];
     unsigned R[TW_MAXD][2];
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
             }
             continue;
         }
-        const unsigned mask = next_pow2(2 * dp) - 1;
+        const unsigned mask = next_pow2(4 * dp) - 1;
         for (int i = lane; i <= (int)mask; i += 32) S.hk[i] = -1;
         for (int i = lane; i < TW_MAXD; i += 32) {
             S.cnt[i] = 0;

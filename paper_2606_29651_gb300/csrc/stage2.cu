@@ -21,8 +21,8 @@ constexpr int AW_WARPS = 8;
 constexpr int AS_MAXD = 256;   // out-degree handled by a 256-thread CTA (k_agg_cta)
 
 struct AggWarpSmem {
-    int hk[2 * AW_MAXD];
-    int hv[2 * AW_MAXD];
+    int hk[4 * AW_MAXD];   // N+(u) hash at load <= 1/4 (most probes are misses)
+    int hv[4 * AW_MAXD];
     long long dc[AW_MAXD];
     SegTab seg;
 };
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
             continue;
         }
         if (!edge_aggregates(g, tcnt, vacc, u, s, dp, lane, 32) || dp < 2) continue;
-        const unsigned mask = next_pow2(2 * dp) - 1;
+        const unsigned mask = next_pow2(4 * dp) - 1;
         for (int i = lane; i <= (int)mask; i += 32) S.hk[i] = -1;
         for (int i = lane; i < AW_MAXD; i += 32) S.dc[i] = 0;
         __syncwarp();
