@@ -226,18 +226,21 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
-                warp_add_int(hit, use_hash ? &cnt[jj] : &tcnt[s + jj], jj, 1);
                 if (use_bits) {
+                    // the upper half of R only; t(u, v) and t(u, w) follow
+                    // from R's rows once it is symmetric
                     const int word = jj * WP + (i >> 5);
                     const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
                     const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
                     if (hit && (peers & lanemask_lt()) == 0) atomicOr(&R[word], bits);
-                    if (hit) atomicOr(&R[i * WP + (jj >> 5)], 1u << (jj & 31));   // and its mirror
+                    if (hit) atomicAdd(&tcnt[pos], 1);
+                    return;
                 }
+                warp_add_int(hit, use_hash ? &cnt[jj] : &tcnt[s + jj], jj, 1);
                 if (!hit) return;
                 atomicAdd(use_hash ? &cnt[i] : &tcnt[s + i], 1);
                 atomicAdd(&tcnt[pos], 1);
-                if (!use_bits) {
+                {
                     // K4 with this triangle (u, v, w): x in N+(w) ∩ N+(u) ∩ N+(v)
                     const int v = g.ncol[s + jj];
                     const int4 rv = g.rinfo[v], rw = g.rinfo[w];
@@ -267,8 +270,35 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
         for (int i = threadIdx.x; i < nloc; i += TC_THREADS)
             if (cnt[i]) atomicAdd(&tcnt[s + i], cnt[i]);
         if (use_bits) {
+            // Mirror R: every 32 x 32 block above the diagonal (and the
+            // diagonal ones) is transposed by one warp with ballots and ORed
+            // into its place below.
+            const int nblk = W * (W + 1) / 2;
+            for (int bidx = wid; bidx < nblk; bidx += NW) {
+                int bj = 0, rem = bidx;
+                while (rem >= W - bj) {
+                    rem -= W - bj;
+                    ++bj;
+                }
+                const int bi = bj + rem;   // block of rows bj, word bi (bi >= bj)
+                const int j = bj * 32 + lane;
+                const unsigned wv = j < dp ? R[j * WP + bi] : 0u;
+                unsigned tv = 0;
+                for (int k = 0; k < 32; ++k) {
+                    const unsigned b = __ballot_sync(FULL, (wv >> k) & 1u);
+                    if (lane == k) tv = b;
+                }
+                const int i = bi * 32 + lane;
+                if (i < dp) {
+                    if (bi == bj) R[i * WP + bj] = wv | tv;
+                    else if (tv) R[i * WP + bj] |= tv;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
             // K4 credits from the symmetric R: warp per row y, one neighbour
-            // z of y per lane, 32 at a time (collected in zb).
+            // z of y per lane, 32 at a time (collected in zb); the row's
+            // popcount is t(u, N+(u)[y]) from the triangles rooted at u.
             for (;;) {
                 int y = 0;
                 if (lane == 0) y = atomicAdd(&work[0], 1);
@@ -285,9 +315,11 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
                     }
                 };
                 int nb = 0;   // entries waiting in zb (warp-uniform)
+                int tuy = 0;  // set bits of row y
                 for (int t = 0; t < W; ++t) {
                     const bool set = (ry[t] >> lane) & 1u;
                     const unsigned bal = __ballot_sync(FULL, set);
+                    tuy += __popc(bal);
                     if (set) zb[nb + __popc(bal & lanemask_lt())] = (unsigned short)(t * 32 + lane);
                     nb += __popc(bal);
                     __syncwarp();
@@ -300,6 +332,7 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
                     }
                 }
                 if (nb) batch(nb);
+                if (lane == 0 && tuy) atomicAdd(&tcnt[s + y], tuy);
                 acc = warp_sum(acc) / 2;   // K4s of u through y
                 if (lane == 0 && acc) {
                     kc[y] = (int)acc;
