@@ -115,25 +115,35 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
 }
 
 // Roots above the warp tier: k_agg_cta (256 threads, dp <= AS_MAXD, about
-// 10 KB of shared memory, several CTAs per SM) and k_agg_big (1024 threads;
-// a hash of N+(u) up to AB_HASH_MAXD, binary searches beyond), from the
-// front and the back of the heavy list.
+// 21 KB of shared memory, several CTAs per SM) and k_agg_big (1024 threads),
+// from the front and the back of the heavy list. Up to AB_BITMAT_MAXD the
+// triangles of u are kept as the upper half of a bit matrix R of N+(u) (as
+// in Stage I): a hit sets its bit and adds t(v, w) - 1 to u; R is then made
+// symmetric, and each y in N+(u) receives the sum over its neighbours z in
+// R of t(u, z) - 1 (t(u, .) cached in shared memory). Above that, a hash of
+// N+(u) up to AB_HASH_MAXD and per-triangle credits; binary searches beyond.
 constexpr int AS_THREADS = 256;
 constexpr int AB_THREADS = 1024;
+constexpr int AB_BITMAT_MAXD = 1152;
+constexpr int AB_BITMAT_HSLOTS = 2048;
 constexpr int AB_HASH_MAXD = 8192;
-constexpr size_t ac_smem(int threads, int maxd) {
-    return (size_t)2 * (2 * maxd) * 4 + (size_t)maxd * 8 + (size_t)(threads / 32) * sizeof(SegTab);
+constexpr int ac_rowstride(int rows) { return ((rows + 31) / 32) | 1; }
+// dc (nloc x 8 B, hash-only mode), hash (2 x hslots ints), t(u, .) cache
+// (rows ints), per warp a segment table and 64 row indices, 4 work words, R.
+constexpr size_t ac_smem(int threads, int hslots, int nloc, int rows) {
+    return (size_t)nloc * 8 + (size_t)2 * hslots * 4 + (size_t)rows * 4 + (size_t)(threads / 32) * (sizeof(SegTab) + 128) +
+           16 + (size_t)rows * ac_rowstride(rows) * 4;
 }
-constexpr size_t AS_SMEM = ac_smem(AS_THREADS, AS_MAXD);
-constexpr size_t AB_SMEM = ac_smem(AB_THREADS, AB_HASH_MAXD);
+constexpr size_t AS_SMEM = ac_smem(AS_THREADS, 2 * AS_MAXD, 0, AS_MAXD);
+constexpr size_t AB_SMEM_BITS = ac_smem(AB_THREADS, AB_BITMAT_HSLOTS, 0, AB_BITMAT_MAXD);
+constexpr size_t AB_SMEM_HASH = ac_smem(AB_THREADS, 2 * AB_HASH_MAXD, AB_HASH_MAXD, 0);
+constexpr size_t AB_SMEM = AB_SMEM_BITS > AB_SMEM_HASH ? AB_SMEM_BITS : AB_SMEM_HASH;
 static_assert(AB_SMEM <= 227 * 1024, "k_agg_big shared memory");
 
-template <int THREADS, int HASH_MAXD, bool BACK>
+template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK>
 __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *vacc, const int *heavy, int nh) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    constexpr int AC_THREADS = THREADS;
-    constexpr int AC_HASH_MAXD = HASH_MAXD;
-    constexpr int NW = AC_THREADS / 32;
+    constexpr int NW = THREADS / 32;
     __shared__ int any_tri;
     const int lane = lane_id(), wid = threadIdx.x >> 5;
     for (int h = blockIdx.x; h < nh; h += gridDim.x) {
@@ -142,23 +152,34 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
         const int s = ru.y, e = ru.z, dp = e - s;
         if (threadIdx.x == 0) any_tri = 0;
         __syncthreads();
-        if (edge_aggregates(g, tcnt, vacc, u, s, dp, threadIdx.x, AC_THREADS) && lane == 0) any_tri = 1;
+        if (edge_aggregates(g, tcnt, vacc, u, s, dp, threadIdx.x, THREADS) && lane == 0) any_tri = 1;
         __syncthreads();
         if (!any_tri) continue;
-        const bool use_hash = dp <= AC_HASH_MAXD;
-        const unsigned H = use_hash ? next_pow2(2 * dp) : 0;
+        const bool use_bits = dp <= BITMAT_MAXD;
+        const bool use_hash = dp <= HASH_MAXD;
+        unsigned H = use_hash ? next_pow2(2 * dp) : 0;
+        if (use_bits && H > (unsigned)BITMAT_HSLOTS) H = BITMAT_HSLOTS;
         const unsigned mask = H ? H - 1 : 0;
-        long long *dc = reinterpret_cast<long long *>(dsm);      // dp (only with the hash)
-        int *hk = reinterpret_cast<int *>(dc + (use_hash ? dp : 0));
+        const int W = (dp + 31) >> 5, WP = W | 1;   // words per row of R, row stride
+        const int nloc = (use_hash && !use_bits) ? dp : 0;
+        const int nrow = use_bits ? dp : 0;
+        long long *dc = reinterpret_cast<long long *>(dsm);   // hash-only mode
+        int *hk = reinterpret_cast<int *>(dc + nloc);
         int *hv = hk + H;
-        SegTab &seg = reinterpret_cast<SegTab *>(hv + H)[wid];
-        if (use_hash) {
-            for (int i = threadIdx.x; i < (int)H; i += AC_THREADS) hk[i] = -1;
-            for (int i = threadIdx.x; i < dp; i += AC_THREADS) dc[i] = 0;
-        }
+        int *T = hv + H;                                       // t(u, N+(u)[i]), bit-matrix mode
+        SegTab *segs = reinterpret_cast<SegTab *>(T + nrow);
+        int *work = reinterpret_cast<int *>(reinterpret_cast<unsigned short *>(segs + NW) + NW * 64);
+        unsigned *R = reinterpret_cast<unsigned *>(work + 4);
+        SegTab &seg = segs[wid];
+        for (int i = threadIdx.x; i < (int)H; i += THREADS) hk[i] = -1;
+        for (int i = threadIdx.x; i < nloc; i += THREADS) dc[i] = 0;
+        for (int i = threadIdx.x; i < nrow; i += THREADS) T[i] = tcnt[s + i];
+        if (use_bits)
+            for (int i = threadIdx.x; i < dp * WP; i += THREADS) R[i] = 0;
+        if (threadIdx.x < 4) work[threadIdx.x] = 0;
         __syncthreads();
         if (use_hash)
-            for (int i = threadIdx.x; i < dp; i += AC_THREADS) hset_insert(hk, hv, mask, g.ncol[s + i], i);
+            for (int i = threadIdx.x; i < dp; i += THREADS) hset_insert(hk, hv, mask, g.ncol[s + i], i);
         const int umax = g.ncol[e - 1];
         __syncthreads();
         long long du12 = 0;
@@ -185,11 +206,18 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
+                if (hit) du12 += tcnt[pos] - 1;   // t(v, w) - 1 -> u
+                if (use_bits) {
+                    const int word = jj * WP + (i >> 5);
+                    const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
+                    const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
+                    if (hit && (peers & lanemask_lt()) == 0) atomicOr(&R[word], bits);
+                    return;
+                }
                 const int tv = hit ? tcnt[s + i] - 1 : 0;
-                warp_add_ll(hit, use_hash ? &dc[jj] : &vacc[g.ncol[s + jj]].D12, jj, tv);
+                warp_add_ll(hit, use_hash ? &dc[jj] : &vacc[g.ncol[s + jj]].D12, jj, tv);   // t(u, w) - 1 -> v
                 if (!hit) return;
-                du12 += tcnt[pos] - 1;
-                const long long tw = tcnt[s + jj] - 1;
+                const long long tw = tcnt[s + jj] - 1;                                      // t(u, v) - 1 -> w
                 if (use_hash) atomicAdd((unsigned long long *)&dc[i], (unsigned long long)tw);
                 else add64(&vacc[w].D12, tw);
             });
@@ -198,21 +226,58 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
         __syncthreads();
         du12 = warp_sum(du12);
         if (lane == 0 && du12) add64(&vacc[u].D12, du12);
-        if (use_hash)
-            for (int i = threadIdx.x; i < dp; i += AC_THREADS)
-                if (dc[i]) add64(&vacc[g.ncol[s + i]].D12, dc[i]);
+        if (use_bits) {
+            // mirror R (a ballot transpose per 32 x 32 block), then y in N+(u)
+            // receives the sum over its neighbours z in R of t(u, z) - 1
+            const int nblk = W * (W + 1) / 2;
+            for (int bidx = wid; bidx < nblk; bidx += NW) {
+                int bj = 0, rem = bidx;
+                while (rem >= W - bj) {
+                    rem -= W - bj;
+                    ++bj;
+                }
+                const int bi = bj + rem;
+                const int jr = bj * 32 + lane;
+                const unsigned wv = jr < dp ? R[jr * WP + bi] : 0u;
+                unsigned tv = 0;
+                for (int k = 0; k < 32; ++k) {
+                    const unsigned b = __ballot_sync(FULL, (wv >> k) & 1u);
+                    if (lane == k) tv = b;
+                }
+                const int ir = bi * 32 + lane;
+                if (ir < dp) {
+                    if (bi == bj) R[ir * WP + bj] = wv | tv;
+                    else if (tv) R[ir * WP + bj] |= tv;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int y = wid; y < dp; y += NW) {
+                const unsigned *ry = R + y * WP;
+                long long c = 0;
+                for (int t = 0; t < W; ++t) {
+                    const int z = t * 32 + lane;
+                    if ((ry[t] >> lane) & 1u) c += T[z] - 1;
+                }
+                c = warp_sum(c);
+                if (lane == 0 && c) add64(&vacc[g.ncol[s + y]].D12, c);
+            }
+        }
+        for (int i = threadIdx.x; i < nloc; i += THREADS)
+            if (dc[i]) add64(&vacc[g.ncol[s + i]].D12, dc[i]);
         __syncthreads();
     }
 }
 
 __global__ void __launch_bounds__(AS_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
                                                         const int *counters) {
-    agg_cta<AS_THREADS, AS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY]);
+    agg_cta<AS_THREADS, AS_MAXD, 2 * AS_MAXD, AS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY]);
 }
 
 __global__ void __launch_bounds__(AB_THREADS) k_agg_big(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
                                                         const int *counters) {
-    agg_cta<AB_THREADS, AB_HASH_MAXD, true>(g, tcnt, vacc, heavy, counters[CNT_AGG_BIG]);
+    agg_cta<AB_THREADS, AB_BITMAT_MAXD, AB_BITMAT_HSLOTS, AB_HASH_MAXD, true>(g, tcnt, vacc, heavy,
+                                                                            counters[CNT_AGG_BIG]);
 }
 
 void launch_stage2(Work &w, cudaStream_t st) {
