@@ -92,6 +92,24 @@ def test_host_entry_rejects_unpinned_tensors(ni):
         ni.count_host(torch.from_numpy(rp), torch.from_numpy(ci))
 
 
+def _with_isolated(rp, ci, extra):
+    rp = np.concatenate([rp, np.full(extra, rp[-1], dtype=rp.dtype)])
+    return rp, ci
+
+
+def test_four_cycle_team_tier_both_modes(ni):
+    # roots with more than 12288 wedges count in a dense row shared by a
+    # cluster of CTAs: K3,9000 (W = 18000 against u ~ 9000) reads the row
+    # back by sweeps; K2,13000 with 200000 isolated vertices (W = 13000,
+    # u ~ 213000) marks first visitors per wedge
+    a, b = 3, 9000
+    assert_same(gpu_count(ni, *gg.complete_bipartite(a, b)), closed_complete_bipartite(a, b), "K3,9000")
+    a, b, extra = 2, 13000, 200000
+    rp, ci = _with_isolated(*gg.complete_bipartite(a, b), extra)
+    exp = np.concatenate([closed_complete_bipartite(a, b), np.zeros((extra, 15), np.int64)])
+    assert_same(gpu_count(ni, rp, ci), exp, "K2,13000 + isolated")
+
+
 def test_empty_and_edgeless(ni):
     rp = np.zeros(6, np.int32)
     assert_same(gpu_count(ni, rp, np.zeros(0, np.int32)), np.zeros((5, 15), np.int64), "edgeless")
@@ -128,6 +146,7 @@ def test_repeated_calls_identical(ni):
 def test_batch_equals_single(ni):
     graphs = [gg.chunglu(int(n), 2.5, 8.0, 100 + i) for i, n in enumerate([50, 3, 1, 700, 2500, 90, 1200])]
     graphs.append(gg.complete(30))
+    graphs.append(gg.complete_bipartite(3, 9000))                    # a root of the 4-cycle team tier
     graphs.append((np.zeros(4, np.int32), np.zeros(0, np.int32)))   # edgeless graph of 3 vertices
     rowptr, colidx, vo, eo = gg.pack(graphs)
     dev = torch.device("cuda:0")

@@ -52,7 +52,8 @@ def _run(lib, fn, rp, ci, status=None):
 @pytest.mark.parametrize("name,make", [
     ("er2000", lambda: gg.er(2000, 0.01, 1)),
     ("rmat12", lambda: gg.rmat(12, 16, seed=3)),
-    ("k2_12000", lambda: gg.complete_bipartite(2, 12000)),   # reaches the dense 4-cycle rows
+    ("k2_12000", lambda: gg.complete_bipartite(2, 12000)),   # the 512-thread 4-cycle tier
+    ("k3_9000", lambda: gg.complete_bipartite(3, 9000)),     # the cluster (dense row) 4-cycle tier
 ])
 def test_noalloc_matches_count_on_two_calls(lib, name, make):
     rp, ci = make()
