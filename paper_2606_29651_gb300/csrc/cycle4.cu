@@ -11,15 +11,17 @@
 //   u gets sum_w C(c_w, 2), w gets C(c_w, 2),
 //   each middle vertex v gets sum over its wedges of (c_w - 1).
 // The wedges through v are the entries of row v below u: a prefix of row v
-// ending at the position of u, which a search of N+(v) finds. Roots
-// are routed by their wedge count W (a count is at most W too): one warp,
-// four warps, a 512-thread CTA, or a CTA with a dense count row in global
-// memory. Tables are open-addressing
-// hash tables in shared memory, either split (key and count arrays) or
-// packed (key << cb | count in one 32-bit word, cb = 32 - bits(n - 1) count
-// bits, usable while UB < 2^cb - 1), which holds twice the keys in the same
-// space. Each table is emptied once per CTA; afterwards a root empties only
-// the slots it filled (kept in a 16-bit `touched` list).
+// ending at the position of u, which a search of N+(v) finds. Roots are
+// routed by their wedge count W (a count is at most W too): one warp
+// (k_c4_warp), four warps (k_c4_midp / k_c4_mid), a 512-thread CTA
+// (k_c4_cta), or a cluster of CTAs sharing a dense count row in global
+// memory (k_c4_team). The other tables are open-addressing hash tables in
+// shared memory, either split (key and count arrays) or packed (key << cb |
+// count in one 32-bit word, cb = 32 - bits(n - 1) count bits, usable while
+// W < 2^cb - 1), which holds twice the keys in the same space. Each table
+// is emptied once per CTA; afterwards a warp sweeps the region its root
+// used, and a CTA empties the slots it filled (kept in a 16-bit `touched`
+// list).
 #include <cooperative_groups.h>
 
 #include "kernels.h"
@@ -28,14 +30,14 @@ namespace niorca {
 
 constexpr int CW_WARPS = 4;
 constexpr int CW_SLOTS = 2048;      // packed
-constexpr int CW_MAXUB = 1536;
+constexpr int CW_MAXW = 1536;
 constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
 constexpr int CM_THREADS = 128;
 constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
-constexpr int CM_MAXUB = 3072;      // split; 6144 when packed
+constexpr int CM_MAXW = 3072;      // split; 6144 when packed
 constexpr int CC_THREADS = 512;
 constexpr int CC_SLOTS = 16384;     // split
-constexpr int CC_MAXUB = 12288;
+constexpr int CC_MAXW = 12288;
 constexpr int CT_THREADS = 1024;   // team tier: CTAs of a cluster share one dense row
 constexpr int CT_CLUSTER = 8;
 constexpr int CT_MAXCH = (1 << 20) / 32;   // chunks of 32 in-neighbours (degree <= 2^20)
@@ -347,10 +349,10 @@ struct __align__(16) C4WarpSmem {
     int dups[2 * CW_DUPS];   // repeated keys of a root and their counts
 };
 
-// One warp per root with W <= maxub (<= CW_MAXUB) that fits a packed table;
+// One warp per root with W <= maxw (<= CW_MAXW) that fits a packed table;
 // other roots are queued for the wider tiers.
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists,
-                                                           int *counters, int maxub, int cb) {
+                                                           int *counters, int maxw, int cb) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
         [&] {
             const int b = ru.x, din = ru.y - ru.x;
             if (din < 2) return;
-            long long ub = 0;   // exact wedge count W of root u
+            long long W = 0;   // exact wedge count W of root u
             Chunk0 c0pre{false, 0, 0, 0, 0};
             if (din <= 32) {   // one chunk: its segment table gives W
                 int st = 0, len = 0;
@@ -389,27 +391,27 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
                 c0pre.len = len;
                 c0pre.total = seg_build(S.seg, st, len, c0pre.pre);
                 c0pre.built = true;
-                ub = c0pre.total;
+                W = c0pre.total;
             } else {
-                for (int p = lane; p < din; p += 32) ub += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
-                ub = warp_sum(ub);
+                for (int p = lane; p < din; p += 32) W += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
+                W = warp_sum(W);
             }
             rv1 = v1 >= 0 ? g.rinfo[v1] : Z;   // next root's in-neighbours, during this walk
             rv1_loaded = true;
-            if (ub < 2) return;
-            if (ub > maxub || ub > pack_lim) {
+            if (W < 2) return;
+            if (W > maxw || W > pack_lim) {
                 if (lane == 0) {
                     int which, list;   // queue counter and list slot (lists + list * n)
-                    if (ub > CC_MAXUB) { which = CNT_C4_GLOBAL; list = 4; }
-                    else if (ub <= 2 * CM_MAXUB && ub <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
-                    else if (ub <= CM_MAXUB) { which = CNT_C4_MID; list = 2; }
+                    if (W > CC_MAXW) { which = CNT_C4_TEAM; list = 4; }
+                    else if (W <= 2 * CM_MAXW && W <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
+                    else if (W <= CM_MAXW) { which = CNT_C4_MID; list = 2; }
                     else { which = CNT_C4_CTA; list = 3; }
                     lists[(size_t)list * g.n + atomicAdd(&counters[which], 1)] = u;
                 }
                 return;
             }
             // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
-            unsigned slots = next_pow2(2 * (unsigned)ub);
+            unsigned slots = next_pow2(2 * (unsigned)W);
             slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
             const PackedTab T{S.t, slots - 1, cb, nullptr};
             c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
@@ -425,12 +427,12 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
 // Roots from a queue, one CTA each. The table (SLOTS split slots, or
 // 2 x SLOTS packed ones) lives in dynamic shared memory and is emptied once
 // per CTA.
-template <int THREADS, int SLOTS, int MAXUB, bool PACKED>
+template <int THREADS, int SLOTS, int MAXW, bool PACKED>
 __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count,
                                          int cb) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
-    constexpr int NT = PACKED ? 2 * MAXUB : MAXUB;   // touched capacity: every key of a root
+    constexpr int NT = PACKED ? 2 * MAXW : MAXW;   // touched capacity: every key of a root
     unsigned *words = reinterpret_cast<unsigned *>(dsm);            // 2 x SLOTS words
     unsigned short *touched = reinterpret_cast<unsigned short *>(words + 2 * SLOTS);
     SegTab *segs = reinterpret_cast<SegTab *>(touched + NT);         // one per warp
@@ -459,31 +461,31 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
     }
 }
 
-constexpr size_t cq_smem(int threads, int slots, int maxub) {
-    // 2 x slots words, 2 x maxub 16-bit touched entries, segments, pv, flags
-    return (size_t)2 * slots * 4 + (size_t)2 * maxub * 2 + (size_t)(threads / 32) * sizeof(SegTab) + 32 * 8 + 16;
+constexpr size_t cq_smem(int threads, int slots, int maxw) {
+    // 2 x slots words, 2 x maxw 16-bit touched entries, segments, pv, flags
+    return (size_t)2 * slots * 4 + (size_t)2 * maxw * 2 + (size_t)(threads / 32) * sizeof(SegTab) + 32 * 8 + 16;
 }
-constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXUB);
-constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXUB);
+constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXW);
+constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXW);
 
 __global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists,
                                                        const int *counters, int cb) {
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
 }
 
 __global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, VAcc *vacc, const int *lists,
                                                         const int *counters, int cb) {
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXUB, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
 }
 
 __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists,
                                                        const int *counters, int cb) {
-    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXUB, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
+    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXW, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
 }
 
 // Zero the dense rows of the team tier (only when that tier has work).
 __global__ void k_c4_zero_dense(int *dense, long long words, const int *counters) {
-    if (counters[CNT_C4_GLOBAL] == 0) return;
+    if (counters[CNT_C4_TEAM] == 0) return;
     int4 *d4 = reinterpret_cast<int4 *>(dense);
     const long long n4 = words / 4;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
@@ -493,7 +495,7 @@ __global__ void k_c4_zero_dense(int *dense, long long words, const int *counters
         dense[i] = 0;
 }
 
-// Roots with W > CC_MAXUB: one cluster of CT_CLUSTER CTAs per root, counting
+// Roots with W > CC_MAXW: one cluster of CT_CLUSTER CTAs per root, counting
 // in a dense row of n ints in global memory that the cluster shares, so
 // that only one row per cluster is live. The root's wedges, in the order
 // of its in-neighbours, are cut into equal slices, one per warp of the
@@ -522,7 +524,7 @@ __global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
     SegTab &seg = segs[wid];
     long long *pv = pvs[wid];
     const int *glob_list = lists + 4 * (size_t)g.n;
-    const int nh = counters[CNT_C4_GLOBAL];
+    const int nh = counters[CNT_C4_TEAM];
     for (int h = team; h < nh; h += teams) {
         const int u = glob_list[h];
         const int4 ru = g.rinfo[u];
@@ -646,9 +648,9 @@ static int packed_count_bits(int n) {
 
 void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
-    const int maxub = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXUB ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXUB;
+    const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
     const int cb = packed_count_bits(w.n);
-    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxub,
+    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
                                                                          cb);
     after_launch(st, K_C4_WARP);
     k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
@@ -663,7 +665,7 @@ void launch_cycle4(Work &w, cudaStream_t st) {
         after_launch(st, K_C4_ZERO);
         k_c4_team<<<w.c4slots * CT_CLUSTER, CT_THREADS, CT_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
                                                                        w.c4dense, w.c4slots);
-        after_launch(st, K_C4_GLOBAL);
+        after_launch(st, K_C4_TEAM);
     }
 }
 

@@ -40,7 +40,7 @@ enum TuneIndex {
     TUNE_GRID_C4 = 3,        // k_c4_warp
     TUNE_GRID_SOLVE = 4,     // k_solve
     TUNE_LONG_ROW_CLASS = 5, // degree class from which a row is relabelled by a whole CTA
-    TUNE_C4_WARP_MAXW = 6,   // largest wedge bound of a 4-cycle root kept in one warp (<= 1536)
+    TUNE_C4_WARP_MAXW = 6,   // largest wedge count W of a 4-cycle root kept in one warp (<= 1536)
     TUNE_WARP_MAXD = 7,      // largest out-degree of a triangle root kept in one warp (<= 64)
     TUNE_COUNT = 8
 };
@@ -48,7 +48,7 @@ enum TuneIndex {
 // Indices into Work::counters.
 // The triangle and aggregate heavy lists hold two tiers each: CTA-sized
 // roots from the front (CNT_*_HEAVY), the largest from the back (CNT_*_BIG).
-enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_GLOBAL = 3, CNT_DMAX = 4, CNT_C4_MID = 5,
+enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_TEAM = 3, CNT_DMAX = 4, CNT_C4_MID = 5,
        CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8 };
 
 constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
@@ -73,7 +73,7 @@ void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *st
 // Kernel ids for the optional per-kernel event timing and launch counting.
 enum KernelId {
     K_CLASS_HIST, K_SCAN, K_CLASS_SCATTER, K_RELABEL_WARP, K_RELABEL_CTA, K_BATCH_SETUP,
-    K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_ZERO, K_C4_GLOBAL,
+    K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_ZERO, K_C4_TEAM,
     K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_COUNT
 };
 const char *kernel_name(int id);
