@@ -163,11 +163,10 @@ __device__ __forceinline__ int seg_build(SegTab &T, int st, int len, int &mypre)
 // windows per round with their loads issued first. The segment of element
 // ws + lane is found without a search: one reduction marks where non-empty
 // segments start inside the window, one ballot counts those that start
-// before it. f(q[U], pos[U], val[U]) runs once per round on every lane
-// (pos < 0: no element; q = owning lane; val = col[pos]).
+// before it. f(valid, q, pos, col[pos]) runs on every lane (q = owning lane).
 template <int U, class F>
-__device__ __forceinline__ void seg_visit_rounds(const int *__restrict__ col, const SegTab &T, int mypre, int mylen,
-                                                 int total, int wbase, int stride, F f) {
+__device__ __forceinline__ void seg_visit(const int *__restrict__ col, const SegTab &T, int mypre, int mylen,
+                                          int total, int wbase, int stride, F f) {
     const int lane = lane_id();
     const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
     for (int w0 = wbase; w0 < total; w0 += U * stride) {
@@ -189,20 +188,9 @@ __device__ __forceinline__ void seg_visit_rounds(const int *__restrict__ col, co
                 val[r] = __ldg(col + pos[r]);
             }
         }
-        f(q, pos, val);
-    }
-}
-
-// The same walk with f(valid, q, pos, col[pos]) called per window, on every
-// lane (q = owning lane).
-template <int U, class F>
-__device__ __forceinline__ void seg_visit(const int *__restrict__ col, const SegTab &T, int mypre, int mylen,
-                                          int total, int wbase, int stride, F f) {
-    seg_visit_rounds<U>(col, T, mypre, mylen, total, wbase, stride,
-                        [&](const int (&q)[U], const int (&pos)[U], const int (&val)[U]) {
 #pragma unroll
-                            for (int r = 0; r < U; ++r) f(pos[r] >= 0, q[r], pos[r], val[r]);
-                        });
+        for (int r = 0; r < U; ++r) f(pos[r] >= 0, q[r], pos[r], val[r]);
+    }
 }
 
 // First position p in [lo, hi) with a[p] >= key (a sorted ascending).

@@ -197,18 +197,6 @@ struct PackedTab {
         }
         return -1;
     }
-    // finishes an add whose first probe, at slot s = fib_slot(w), found
-    // prev != EMPTY (the caller issued that compare-and-swap)
-    __device__ __forceinline__ int add_after(int w, unsigned s, unsigned prev) const {
-        const unsigned key = static_cast<unsigned>(w);
-        for (unsigned probe = 0; probe < mask; ++probe) {
-            if ((prev >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
-            s = next_probe(s, probe, w, mask);
-            prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
-            if (prev == EMPTY) return (int)s;
-        }
-        return -1;
-    }
     __device__ __forceinline__ int get(int w) const {
         const unsigned key = static_cast<unsigned>(w);
         unsigned s = fib_slot(w, mask);
@@ -229,42 +217,6 @@ struct PackedTab {
         for (int i = tid; i < (int)(mask + 1) / 4; i += nthreads) t4[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
     }
 };
-
-// Counts the wedges of root u into a packed table in the calling warp: the
-// first compare-and-swap of all U windows of a round is issued before any is
-// resolved, so that U of them are in flight per lane. Sets dup when a key
-// repeats (a 4-cycle).
-template <int U>
-__device__ __forceinline__ void insert_wedges(const Graph &g, int u, int b, int din, SegTab &T, const PackedTab &tab,
-                                              bool &dup, Chunk0 c0pre) {
-    for (int cb = 0; cb < din; cb += 32) {
-        int v, len, pre, total;
-        if (c0pre.built) {
-            v = c0pre.v, len = c0pre.len, pre = c0pre.pre, total = c0pre.total;
-            c0pre.built = false;
-        } else {
-            total = wedge_chunk(g, u, b, din, cb, T, v, len, pre);
-        }
-        seg_visit_rounds<U>(g.ncol, T, pre, len, total, 0, 32,
-                            [&](const int (&q)[U], const int (&pos)[U], const int (&val)[U]) {
-                                unsigned s[U], prev[U];
-#pragma unroll
-                                for (int r = 0; r < U; ++r) {
-                                    s[r] = 0;
-                                    prev[r] = EMPTY;
-                                    if (pos[r] >= 0) {
-                                        s[r] = fib_slot(val[r], tab.mask);
-                                        prev[r] = atomicCAS(&tab.t[s[r]], EMPTY,
-                                                            (static_cast<unsigned>(val[r]) << tab.cb) | 1u);
-                                    }
-                                }
-#pragma unroll
-                                for (int r = 0; r < U; ++r)
-                                    if (prev[r] != EMPTY) dup |= tab.add_after(val[r], s[r], prev[r]) == -1;
-                            });
-        __syncwarp();
-    }
-}
 
 // Counts all wedges of u into the table and credits every 4-cycle rooted at
 // u. Every thread of the group (one warp, or a CTA with CTA = true) calls it.
@@ -302,8 +254,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
             T.touched[base + __popc(fresh & lanemask_lt())] = (unsigned short)slot;
         }
     };
-    if constexpr (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
-    else insert_wedges<4>(g, u, b, din, seg, T, dup_l, c0pre);
+    if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
+    else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {}, c0pre);
     sync();
     const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
     bool sweep = CTA ? flags[1] != 0 : false;
