@@ -80,7 +80,7 @@ __device__ __forceinline__ void to_induced(long long *p) {
 // order puts them last): one warp per vertex. Every other vertex is solved in
 // groups of 32 consecutive caller ids: each lane loads its vertex's row bounds
 // and accumulators up front, the warp sums S1 and A1 over the neighbours of
-// each of the 32 in turn (coalesced gathers, four vertices in flight), each
+// each of the 32 in turn (coalesced gathers, two vertices in flight), each
 // lane solves its own vertex, and the warp writes the group's 32 output rows
 // (3840 contiguous bytes) with coalesced stores through shared memory, which
 // also suits an output buffer in host memory.
@@ -133,34 +133,29 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(Graph g, const VAcc 
         }
         long long mS1 = 0, mA1 = 0;   // this lane's vertex
         const int cnt = min(32, g.n - xo0);
-        constexpr int V = 4;          // vertices whose gathers are in flight together
-        for (int k = 0; k < cnt; k += V) {
-            int bb[V], ee[V], len = 0;
-#pragma unroll
-            for (int r = 0; r < V; ++r) {
-                const int src = (k + r) & 31;
-                bb[r] = __shfl_sync(FULL, rx.x, src);
-                ee[r] = __shfl_sync(FULL, rx.z, src);
-                if (k + r >= cnt) ee[r] = bb[r];
-                len = max(len, ee[r] - bb[r]);
+        for (int k = 0; k < cnt; k += 2) {
+            const int b0 = __shfl_sync(FULL, rx.x, k), e0 = __shfl_sync(FULL, rx.z, k);
+            const int b1 = __shfl_sync(FULL, rx.x, k + 1 < 32 ? k + 1 : 31);
+            const int e1 = k + 1 < cnt ? __shfl_sync(FULL, rx.z, k + 1) : b1;
+            long long s0 = 0, t0 = 0, s1 = 0, t1 = 0;
+            for (int off = lane; off < max(e0 - b0, e1 - b1); off += 32) {
+                if (b0 + off < e0) {
+                    const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[b0 + off]]);
+                    s0 += sa.x;
+                    t0 += sa.y;
+                }
+                if (b1 + off < e1) {
+                    const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[b1 + off]]);
+                    s1 += sa.x;
+                    t1 += sa.y;
+                }
             }
-            long long ss[V], tt[V];
-#pragma unroll
-            for (int r = 0; r < V; ++r) ss[r] = tt[r] = 0;
-            for (int off = lane; off < len; off += 32) {
-#pragma unroll
-                for (int r = 0; r < V; ++r)
-                    if (bb[r] + off < ee[r]) {
-                        const longlong2 sa = *reinterpret_cast<const longlong2 *>(&vacc[g.ncol[bb[r] + off]]);
-                        ss[r] += sa.x;
-                        tt[r] += sa.y;
-                    }
-            }
-#pragma unroll
-            for (int r = 0; r < V; ++r) {
-                const long long s0 = warp_sum(ss[r]), t0 = warp_sum(tt[r]);
-                if (lane == k + r) { mS1 = s0; mA1 = t0; }
-            }
+            s0 = warp_sum(s0);
+            t0 = warp_sum(t0);
+            s1 = warp_sum(s1);
+            t1 = warp_sum(t1);
+            if (lane == k) { mS1 = s0; mA1 = t0; }
+            if (lane == k + 1) { mS1 = s1; mA1 = t1; }
         }
         if (have) solve_write(rx.z - rx.x, a, mS1, mA1, induced, ob + lane * 15);
         __syncwarp();

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
             }
             int mypre;
             const int total = seg_build(S.seg, vs, len, mypre);
-            seg_visit<4>(g.ncol, S.seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            seg_visit<2>(g.ncol, S.seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? hset_find(S.hk, S.hv, mask, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
