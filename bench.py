@@ -211,13 +211,28 @@ def measured_peaks() -> dict:
 
 
 def cpu_baseline(rowptr, colidx, edges) -> dict:
+    """The oracle on the host cores: the whole workload graph with all
+    threads, and one thread on a bounded sample of the same generator."""
+    import graphgen as gg
     import oracle
+    cores = oracle.max_threads()
     t0 = time.perf_counter()
     oracle.count(rowptr, colidx)
     dt = time.perf_counter() - t0
-    return {"value": edges / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    srp, sci = gg.er_mean_degree(REF_SAMPLE_N, MEAN_DEG, 1)
+    oracle.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        oracle.count(srp, sci)
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(cores)
+    return {"value": edges / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"the whole workload graph ({edges} edges), three-stage CPU oracle, all host threads, "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s",
+            "single_thread": {"value": (len(sci) // 2) / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"ER G(n={REF_SAMPLE_N}, mean degree {MEAN_DEG}), {len(sci) // 2} edges, "
+                                        f"{dt1:.1f} s"}}
 
 
 def dist_setup():
