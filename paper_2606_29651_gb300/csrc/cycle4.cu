@@ -29,8 +29,8 @@
 namespace niorca {
 
 constexpr int CW_WARPS = 4;
-constexpr int CW_SLOTS = 1792;      // packed, per warp (7 KB: 7 CTAs of 4 warps per SM)
-constexpr int CW_MAXW = 1344;       // largest W of the warp tier (load <= 3/4)
+constexpr int CW_SLOTS = 1536;      // packed, per warp (6 KB: 8 CTAs of 4 warps per SM)
+constexpr int CW_MAXW = 1152;       // largest W of the warp tier (load <= 3/4)
 constexpr int CW_LSLOTS = 2048;     // packed, per warp, k_c4_warpl
 constexpr int CW_LMAXW = 1536;      // largest W of k_c4_warpl
 constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
@@ -278,10 +278,9 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         // each in-neighbour. More repeated keys: the middle walk below.
         long long su = 0;
         int nd = 0;
-        for (int i0 = 0; i0 < nt; i0 += 32) {   // all lanes take part in every ballot
-            const int i = i0 + lane;
-            const int c = (i >= nt || T.empty(i)) ? 0 : T.cnt(i);
-            const unsigned rep = __ballot_sync(FULL, c >= 2);
+        for (int i = lane; i < nt; i += 32) {
+            const int c = T.empty(i) ? 0 : T.cnt(i);
+            const unsigned rep = __ballot_sync(FULL, c >= 2);   // nt is a multiple of 32
             if (c >= 2) {
                 const int w = T.key(i);
                 su += c2(c);
@@ -461,7 +460,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warpl(Graph g, VAcc *vacc,
         for (int p = lane; p < din; p += 32) W += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
         W = warp_sum(W);
         unsigned slots = next_pow2(2 * (unsigned)W);
-        slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_LSLOTS ? CW_LSLOTS : slots);
+        slots = slots > CW_LSLOTS ? CW_LSLOTS : slots;
         const PackedTab T{S.t, slots, cb, nullptr};
         c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups);
     }
