@@ -76,8 +76,8 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     B_c4  = 4 * number of wedges u - v - w with v, w below u (cycle roots)
     B_csr = 4 (n + 1) + 4 m, B_out = 120 n.
     A root's wedges (or triangle probes) count for the tier kernel that
-    takes it: 4-cycle roots by their wedge count W (warp <= 1152 and warpl
-    <= 1536 with packed tables, packed mid <= 6144, split mid <= 3072, cta <= 12288, else
+    takes it: 4-cycle roots by their wedge count W (warp <= 1152 with a
+    packed table, packed mid <= 6144, split mid <= 3072, cta <= 12288, else
     global), triangle roots by out-degree (warp <= 64, cta <= 256, else
     big).
     """
@@ -109,11 +109,10 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     live = (din >= 2) & (w_root >= 2)
     pack_lim = (1 << (32 - int(n - 1).bit_length())) - 2     # packed tables hold counts below this
     warp = live & (w_root <= min(c4_warp_ub, 1152, pack_lim))
-    warpl = live & ~warp & (w_root <= min(1536, pack_lim))
-    midp = live & ~warp & ~warpl & (w_root <= 6144) & (w_root <= pack_lim)
-    mid = live & ~warp & ~warpl & ~midp & (w_root <= 3072)
-    cta = live & ~warp & ~warpl & ~midp & ~mid & (w_root <= 12288)
-    tiers = {"k_c4_warp": warp, "k_c4_warpl": warpl, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
+    midp = live & ~warp & (w_root <= 6144) & (w_root <= pack_lim)
+    mid = live & ~warp & ~midp & (w_root <= 3072)
+    cta = live & ~warp & ~midp & ~mid & (w_root <= 12288)
+    tiers = {"k_c4_warp": warp, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
              "k_c4_team": live & (w_root > 12288)}
     w_c4 = int(w_root.sum())
     # B_k4 = 4 * sum over oriented edges (u, v) and w in S = N+(u) ∩ N+(v) of

@@ -31,8 +31,6 @@ namespace niorca {
 constexpr int CW_WARPS = 4;
 constexpr int CW_SLOTS = 1536;      // packed, per warp (6 KB: 8 CTAs of 4 warps per SM)
 constexpr int CW_MAXW = 1152;       // largest W of the warp tier (load <= 3/4)
-constexpr int CW_LSLOTS = 2048;     // packed, per warp, k_c4_warpl
-constexpr int CW_LMAXW = 1536;      // largest W of k_c4_warpl
 constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
 constexpr int CM_THREADS = 128;
 constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
@@ -354,9 +352,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
 
 constexpr int CW_MIN_SLOTS = 64;
 
-template <int SLOTS>
 struct __align__(16) C4WarpSmem {
-    unsigned t[SLOTS];
+    unsigned t[CW_SLOTS];
     SegTab seg;
     long long pv[32];
     int dups[2 * CW_DUPS];   // repeated keys of a root and their counts
@@ -366,8 +363,8 @@ struct __align__(16) C4WarpSmem {
 // other roots are queued for the wider tiers.
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists,
                                                            int *counters, int maxw, int cb) {
-    __shared__ C4WarpSmem<CW_SLOTS> sm_all[CW_WARPS];
-    C4WarpSmem<CW_SLOTS> &S = sm_all[threadIdx.x >> 5];
+    __shared__ C4WarpSmem sm_all[CW_WARPS];
+    C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -415,8 +412,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             if (W > maxw || W > pack_lim) {
                 if (lane == 0) {
                     int which, list;   // queue counter and list slot (lists + list * n)
-                    if (W <= CW_LMAXW && W <= pack_lim) { which = CNT_C4_WARPL; list = 6; }
-                    else if (W > CC_MAXW) { which = CNT_C4_TEAM; list = 4; }
+                    if (W > CC_MAXW) { which = CNT_C4_TEAM; list = 4; }
                     else if (W <= 2 * CM_MAXW && W <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
                     else if (W <= CM_MAXW) { which = CNT_C4_MID; list = 2; }
                     else { which = CNT_C4_CTA; list = 3; }
@@ -435,34 +431,6 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
         ru1 = ru2;
         v0 = v1;
         rv0 = rv1;
-    }
-}
-
-// Queued roots with CW_MAXW (or the tuned maxw) < W <= CW_LMAXW: one warp
-// each, with 2048-slot tables (24 warps per SM; the few roots this large
-// would otherwise cost every k_c4_warp a larger table).
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warpl(Graph g, VAcc *vacc, const int *lists,
-                                                            const int *counters, int cb) {
-    __shared__ C4WarpSmem<CW_LSLOTS> sm_all[CW_WARPS];
-    C4WarpSmem<CW_LSLOTS> &S = sm_all[threadIdx.x >> 5];
-    const int lane = lane_id();
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    const int *list = lists + 6 * (size_t)g.n;
-    const int nq = counters[CNT_C4_WARPL];
-    PackedTab{S.t, CW_LSLOTS, cb, nullptr}.clear_all(lane, 32);
-    __syncwarp();
-    for (int h = gw; h < nq; h += nw) {
-        const int u = list[h];
-        const int4 ru = g.rinfo[u];
-        const int b = ru.x, din = ru.y - ru.x;
-        long long W = 0;
-        for (int p = lane; p < din; p += 32) W += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
-        W = warp_sum(W);
-        unsigned slots = next_pow2(2 * (unsigned)W);
-        slots = slots > CW_LSLOTS ? CW_LSLOTS : slots;
-        const PackedTab T{S.t, slots, cb, nullptr};
-        c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups);
     }
 }
 
@@ -695,8 +663,6 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
                                                                          cb);
     after_launch(st, K_C4_WARP);
-    k_c4_warpl<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, cb);
-    after_launch(st, K_C4_WARPL);
     k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MIDP);
     k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);

@@ -21,7 +21,7 @@ struct Work {
     int *tcnt = nullptr;     // triangle count of each out-entry (u, v), u < v; m
     VAcc *vacc = nullptr;    // per-vertex accumulators, n
     int *scan_part = nullptr;// scan block partials
-    int *lists = nullptr;    // heavy-vertex lists, NLISTS x n
+    int *lists = nullptr;    // heavy-vertex lists, 6 x n
     int *counters = nullptr; // list lengths and flags, 16 ints
     int *c4dense = nullptr;  // dense counting rows for the largest 4-cycle roots
     int c4slots = 0;         // rows in c4dense (each n ints), one per team of CTAs
@@ -40,7 +40,7 @@ enum TuneIndex {
     TUNE_GRID_C4 = 3,        // k_c4_warp
     TUNE_GRID_SOLVE = 4,     // k_solve
     TUNE_LONG_ROW_CLASS = 5, // degree class from which a row is relabelled by a whole CTA
-    TUNE_C4_WARP_MAXW = 6,   // largest wedge count W of a root counted by k_c4_warp (<= 1152)
+    TUNE_C4_WARP_MAXW = 6,   // largest wedge count W of a 4-cycle root kept in one warp (<= 1152)
     TUNE_WARP_MAXD = 7,      // largest out-degree of a triangle root kept in one warp (<= 64)
     TUNE_COUNT = 8
 };
@@ -49,9 +49,8 @@ enum TuneIndex {
 // The triangle and aggregate heavy lists hold two tiers each: CTA-sized
 // roots from the front (CNT_*_HEAVY), the largest from the back (CNT_*_BIG).
 enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_TEAM = 3, CNT_DMAX = 4, CNT_C4_MID = 5,
-       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8, CNT_C4_WARPL = 9 };
+       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8 };
 
-constexpr int NLISTS = 7;           // vertex lists of n ints each (work queues of the tiers)
 constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
 constexpr int SCAN_TILE = 4096;      // elements per scan block
 constexpr int LONG_ROW_CLASS = 32;   // deg_class(512): rows from here on get a CTA each
@@ -75,7 +74,7 @@ void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *st
 enum KernelId {
     K_CLASS_HIST, K_SCAN, K_CLASS_SCATTER, K_RELABEL_WARP, K_RELABEL_CTA, K_BATCH_SETUP,
     K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_ZERO, K_C4_TEAM,
-    K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_C4_WARPL, K_COUNT
+    K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_COUNT
 };
 const char *kernel_name(int id);
 

@@ -37,7 +37,7 @@ thread_local Timeline *t_cur = nullptr;
 const char *const kNames[K_COUNT] = {
     "k_class_hist", "k_scan", "k_class_scatter", "k_relabel_rows_warp", "k_relabel_rows_cta", "k_batch_setup",
     "k_tri_warp", "k_tri_cta", "k_agg_warp", "k_agg_cta", "k_c4_warp", "k_c4_cta", "k_c4_zero_dense",
-    "k_c4_team", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big", "k_c4_warpl"};
+    "k_c4_team", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big"};
 }  // namespace
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
@@ -159,7 +159,7 @@ Layout plan(long long n, long long m, int num_sms, bool batch) {
     L.vacc = take(sizeof(VAcc) * n);
     const size_t sp1 = scan_partials(NCLASS * nt), sp2 = scan_partials(n);
     L.scan_part = take(4 * (sp1 > sp2 ? sp1 : sp2));
-    L.lists = take(4 * NLISTS * n);
+    L.lists = take(4 * 6 * n);
     L.counters = take(4 * 16);
     L.c4dense = take(4 * c4_dense_words(L.c4slots, n));
     L.vrange = batch ? take(8 * n) : 0;

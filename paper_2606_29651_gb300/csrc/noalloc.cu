@@ -90,7 +90,7 @@ size_t carve(unsigned char *base, long long n, long long m, int slots, Work *w) 
     w->vacc = reinterpret_cast<VAcc *>(take(sizeof(VAcc) * n));
     const size_t sp1 = scan_partials(NCLASS * nt), sp2 = scan_partials(n);
     w->scan_part = reinterpret_cast<int *>(take(4 * (sp1 > sp2 ? sp1 : sp2)));
-    w->lists = reinterpret_cast<int *>(take(4 * NLISTS * n));
+    w->lists = reinterpret_cast<int *>(take(4 * 6 * n));
     w->counters = reinterpret_cast<int *>(take(4 * 16));
     w->c4dense = reinterpret_cast<int *>(take(4 * c4_dense_words(slots, n)));
     w->c4slots = slots;
