@@ -76,7 +76,7 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     B_c4  = 4 * number of wedges u - v - w with v, w below u (cycle roots)
     B_csr = 4 (n + 1) + 4 m, B_out = 120 n.
     A root's wedges (or triangle probes) count for the tier kernel that
-    takes it: 4-cycle roots by their wedge count W (warp <= 1152 with a
+    takes it: 4-cycle roots by their wedge count W (warp <= 1536 with a
     packed table, packed mid <= 6144, split mid <= 3072, cta <= 12288, else
     global), triangle roots by out-degree (warp <= 64, cta <= 256, else
     big).
@@ -108,7 +108,7 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     din = np.bincount(rd2[sel], minlength=n)
     live = (din >= 2) & (w_root >= 2)
     pack_lim = (1 << (32 - int(n - 1).bit_length())) - 2     # packed tables hold counts below this
-    warp = live & (w_root <= min(c4_warp_ub, 1152, pack_lim))
+    warp = live & (w_root <= min(c4_warp_ub, pack_lim))
     midp = live & ~warp & (w_root <= 6144) & (w_root <= pack_lim)
     mid = live & ~warp & ~midp & (w_root <= 3072)
     cta = live & ~warp & ~midp & ~mid & (w_root <= 12288)

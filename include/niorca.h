@@ -206,8 +206,7 @@ int32_t niorca_version(void);
  *         solve kernels (1..64; defaults 16, 8, 8, 16, 8)
  *   5     degree class from which a row is relabelled by a whole CTA
  *         (1..127; default 32, i.e. degree >= 512)
- *   6     largest wedge count W of a 4-cycle root handled by one warp (2..1536;
- *         values above 1152 act as 1152)
+ *   6     largest wedge count W of a 4-cycle root handled by one warp (2..1536)
  *   7     largest out-degree of a triangle root handled by one warp (2..64)
  * Any setting gives the same counts; only the speed changes. Returns
  * NIORCA_EINVAL (and changes nothing) for a value out of range.

@@ -28,7 +28,7 @@ SEARCH = {
     "grid_agg": (4, 8, 16),
     "grid_solve": (4, 8, 16),
     "warp_maxd": (32, 64),
-    "c4_warp_maxw": (512, 768, 1152),
+    "c4_warp_maxw": (512, 1024, 1536),
     "long_row_class": (24, 28, 32, 36),   # rows of degree >= 128, 256, 512, 1024 get a CTA
 }
 

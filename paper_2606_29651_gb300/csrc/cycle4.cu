@@ -29,8 +29,8 @@
 namespace niorca {
 
 constexpr int CW_WARPS = 4;
-constexpr int CW_SLOTS = 1536;      // packed, per warp (6 KB: 8 CTAs of 4 warps per SM)
-constexpr int CW_MAXW = 1152;       // largest W of the warp tier (load <= 3/4)
+constexpr int CW_SLOTS = 2048;      // packed
+constexpr int CW_MAXW = 1536;
 constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
 constexpr int CM_THREADS = 128;
 constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
@@ -169,7 +169,6 @@ struct SplitTab {
         }
         return 0;
     }
-    __device__ __forceinline__ int slots() const { return (int)mask + 1; }
     __device__ __forceinline__ bool empty(int s) const { return hk[s] == -1; }
     __device__ __forceinline__ int key(int s) const { return hk[s]; }
     __device__ __forceinline__ int cnt(int s) const { return hc[s]; }
@@ -181,50 +180,41 @@ struct SplitTab {
 
 // Packed table: one word (w << cb) | count per slot, EMPTY when free. A
 // count never reaches 2^cb - 1 (the caller ensures W < 2^cb - 1), so a full
-// word is never EMPTY. Any number n of slots (a multiple of 4): a hash is
-// mapped onto [0, n) by the high half of its product with n; the probe
-// sequence is the first hash, the second hash, then linear with wrap-around.
+// word is never EMPTY.
 struct PackedTab {
     unsigned *t;
-    unsigned n;
+    unsigned mask;
     int cb;
     unsigned short *touched;   // slots filled (CTA groups)
-    __device__ __forceinline__ unsigned first(int w) const {
-        return __umulhi(static_cast<unsigned>(w) * 0x9E3779B1u, n);
-    }
-    __device__ __forceinline__ unsigned next(unsigned s, unsigned probe, int w) const {
-        return probe == 0 ? __umulhi(static_cast<unsigned>(w) * 0x85EBCA77u, n) : (s + 1 == n ? 0 : s + 1);
-    }
     __device__ __forceinline__ int add(int w) const {
         const unsigned key = static_cast<unsigned>(w);
-        unsigned s = first(w);
-        for (unsigned probe = 0; probe < n; ++probe) {
+        unsigned s = fib_slot(w, mask);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
             const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
             if (prev == EMPTY) return (int)s;
             if ((prev >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
-            s = next(s, probe, w);
+            s = next_probe(s, probe, w, mask);
         }
         return -1;
     }
     __device__ __forceinline__ int get(int w) const {
         const unsigned key = static_cast<unsigned>(w);
-        unsigned s = first(w);
-        for (unsigned probe = 0; probe < n; ++probe) {
+        unsigned s = fib_slot(w, mask);
+        for (unsigned probe = 0; probe <= mask; ++probe) {
             const unsigned cur = t[s];
             if (cur == EMPTY) return 0;
             if ((cur >> cb) == key) return (int)(cur & ((1u << cb) - 1));
-            s = next(s, probe, w);
+            s = next_probe(s, probe, w, mask);
         }
         return 0;
     }
-    __device__ __forceinline__ int slots() const { return (int)n; }
     __device__ __forceinline__ bool empty(int s) const { return t[s] == EMPTY; }
     __device__ __forceinline__ int key(int s) const { return (int)(t[s] >> cb); }
     __device__ __forceinline__ int cnt(int s) const { return (int)(t[s] & ((1u << cb) - 1)); }
     __device__ __forceinline__ void clear(int s) const { t[s] = EMPTY; }
     __device__ __forceinline__ void clear_all(int tid, int nthreads) const {
         uint4 *t4 = reinterpret_cast<uint4 *>(t);
-        for (int i = tid; i < (int)n / 4; i += nthreads) t4[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+        for (int i = tid; i < (int)(mask + 1) / 4; i += nthreads) t4[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
     }
 };
 
@@ -267,7 +257,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
     else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {}, c0pre);
     sync();
-    const int nt = CTA ? flags[0] : T.slots();   // entries of the list, or slots swept
+    const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
     bool sweep = CTA ? flags[1] != 0 : false;
     if (!CTA && __any_sync(FULL, dup_l)) {
         // A warp sweeps its table for the repeated keys (count >= 2), credits
@@ -369,7 +359,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
-    PackedTab{S.t, CW_SLOTS, cb, nullptr}.clear_all(lane, 32);
+    PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
     __syncwarp();
     // Software pipeline over the warp's roots u, u + nw, u + 2 nw: row bounds
     // are loaded two roots ahead, the first 32 in-neighbours and their row
@@ -423,7 +413,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
             unsigned slots = next_pow2(2 * (unsigned)W);
             slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
-            const PackedTab T{S.t, slots, cb, nullptr};
+            const PackedTab T{S.t, slots - 1, cb, nullptr};
             c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
         }();
         if (!rv1_loaded) rv1 = v1 >= 0 ? g.rinfo[v1] : Z;
@@ -461,7 +451,7 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
         const int u = list[h];
         const int4 ru = g.rinfo[u];
         if (PACKED) {
-            const PackedTab T{words, 2 * SLOTS, cb, touched};
+            const PackedTab T{words, 2 * SLOTS - 1, cb, touched};
             c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
         } else {
             const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS - 1,

@@ -40,7 +40,7 @@ enum TuneIndex {
     TUNE_GRID_C4 = 3,        // k_c4_warp
     TUNE_GRID_SOLVE = 4,     // k_solve
     TUNE_LONG_ROW_CLASS = 5, // degree class from which a row is relabelled by a whole CTA
-    TUNE_C4_WARP_MAXW = 6,   // largest wedge count W of a 4-cycle root kept in one warp (<= 1152)
+    TUNE_C4_WARP_MAXW = 6,   // largest wedge count W of a 4-cycle root kept in one warp (<= 1536)
     TUNE_WARP_MAXD = 7,      // largest out-degree of a triangle root kept in one warp (<= 64)
     TUNE_COUNT = 8
 };
