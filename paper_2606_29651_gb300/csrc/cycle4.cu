@@ -266,9 +266,10 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         // each in-neighbour. More repeated keys: the middle walk below.
         long long su = 0;
         int nd = 0;
-        for (int i = lane; i < nt; i += 32) {
-            const int c = T.empty(i) ? 0 : T.cnt(i);
-            const unsigned rep = __ballot_sync(FULL, c >= 2);   // nt is a multiple of 32
+        for (int i0 = 0; i0 < nt; i0 += 32) {   // all lanes take part in every ballot
+            const int i = i0 + lane;
+            const int c = (i >= nt || T.empty(i)) ? 0 : T.cnt(i);
+            const unsigned rep = __ballot_sync(FULL, c >= 2);
             if (c >= 2) {
                 const int w = T.key(i);
                 su += c2(c);
