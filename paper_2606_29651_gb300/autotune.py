@@ -22,7 +22,7 @@ import torch
 from . import _lib
 
 SEARCH = {
-    "grid_c4": (4, 8, 16, 32),
+    "grid_c4": (3, 6, 12, 18),
     "grid_tri": (2, 4, 8, 16),
     "grid_relabel": (4, 8, 16),
     "grid_agg": (4, 8, 16),

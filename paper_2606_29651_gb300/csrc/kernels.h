@@ -27,7 +27,7 @@ struct Work {
     int c4slots = 0;         // rows in c4dense (each n ints), one per team of CTAs
     int *status = nullptr;   // device status word (not part of the carve)
     int num_sms = 0;
-    int tune[8] = {16, 8, 8, 16, 8, 32, 1536, 64};  // see TuneIndex
+    int tune[8] = {16, 8, 8, 6, 8, 32, 1536, 64};  // see TuneIndex
     int induced = 0;         // write induced instead of non-induced counts
 };
 

@@ -96,7 +96,7 @@ struct DeviceState {
     cudaMemPool_t pool = nullptr;
     int *status = nullptr;
     int num_sms = 0;
-    int tune[TUNE_COUNT] = {16, 8, 8, 16, 8, 32, 1536, 64};
+    int tune[TUNE_COUNT] = {16, 8, 8, 6, 8, 32, 1536, 64};
 };
 
 constexpr int MAX_DEVICES = 64;
