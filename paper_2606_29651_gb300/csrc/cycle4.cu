@@ -82,9 +82,9 @@ __device__ __forceinline__ int wedge_chunk(const Graph &g, int u, int b, int din
     return seg_build(T, st, len, pre);
 }
 
-// Walks the wedges of root u (in-neighbours b .. b + din of row u), one warp
-// per chunk of 32 in-neighbours (chunks c0, c0 + cstep, ...): f(act, q, w) on
-// every lane, act meaning that w is a wedge end through the v owned by lane
+// Walks the wedges of root u (in-neighbours b .. b + din of row u) in the
+// calling warp, chunk by chunk of 32 in-neighbours: f(act, q, w) on every
+// lane, act meaning that w is a wedge end through the v owned by lane
 // q; then done(v) per chunk.
 // A root with at most 32 in-neighbours has one chunk; its table may be
 // built already (built = true: T holds it, v/len/pre/total are the lane's).
@@ -94,9 +94,9 @@ struct Chunk0 {
 };
 
 template <class F, class D>
-__device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, int c0, int cstep,
-                                            SegTab &T, F f, D done, Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
-    for (int cb = c0 * 32; cb < din; cb += cstep * 32) {
+__device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, SegTab &T, F f, D done,
+                                            Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
+    for (int cb = 0; cb < din; cb += 32) {
         int v, len, pre, total;
         if (c0pre.built) {
             v = c0pre.v, len = c0pre.len, pre = c0pre.pre, total = c0pre.total;
@@ -255,7 +255,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         }
     };
     if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
-    else walk_wedges(g, u, b, din, 0, 1, seg, insert, [](int) {}, c0pre);
+    else walk_wedges(g, u, b, din, seg, insert, [](int) {}, c0pre);
     sync();
     const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
     bool sweep = CTA ? flags[1] != 0 : false;
@@ -325,7 +325,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
             pv[lane] = 0;
         };
         if (CTA) walk_wedges_cta<true>(g, u, b, din, wid, nw, seg, middle, flush);
-        else walk_wedges(g, u, b, din, 0, 1, seg, middle, flush);
+        else walk_wedges(g, u, b, din, seg, middle, flush);
         sync();
     }
     if (CTA) {
