@@ -6,19 +6,20 @@
 // way with ids). For a root u the kernel loads N+(u) into a shared-memory
 // hash table, streams N+(v) of every v in N+(u) across the lanes of a warp
 // (the lists of several v are concatenated so that every lane is busy) and
-// probes each element. A hit is a triangle (u, v, w):
-//   t(u,v) and t(u,w) are counted in shared memory and added once per root,
-//   t(v,w) is added to global memory at the position of w in row v.
-// The hits also fill R, the adjacency bit-matrix of N+(u): in the warp tier
-// oriented upwards (R[j] bit i <=> N+(u)[i] in N+(N+(u)[j])), so that a K4
-// u < v < w < x is a triangle (j, i) of R together with a common bit of R[j]
-// and R[i] -- Algorithm 2's pairwise test over `neigh` done as word-wide bit
-// operations. In the CTA tiers R is kept symmetric: the K4s of u through
-// y = N+(u)[y] are the triangles of R at y, and twice their number is the sum
-// over the neighbours z of y in R of popc(R[y] & R[z]). A warp takes a row
-// and its lanes one neighbour z each, with the same word loop on every lane,
-// so the cost follows the edges of R and not the (much larger) number of K4s
-// of dense hub neighbourhoods.
+// probes each element. A hit is a triangle (u, v, w): t(v,w) is added to
+// global memory at the position of w in row v, and the hit sets bit i of row
+// j of R, the adjacency bit-matrix of N+(u) oriented upwards (R[j] bit i <=>
+// N+(u)[i] in N+(N+(u)[j]), v = N+(u)[j], w = N+(u)[i]).
+// In the warp tier t(u,v) and t(u,w) are also counted in shared memory per
+// hit, and a K4 u < v < w < x is a triangle (j, i) of R together with a
+// common bit of R[j] and R[i] -- Algorithm 2's pairwise test over `neigh`
+// done as word-wide bit operations. In the CTA tiers R is mirrored after the
+// expansion (a ballot transpose per 32 x 32 block), t(u, N+(u)[y]) is the
+// popcount of row y, and the K4s of u through y are the triangles of R at y:
+// twice their number is the sum over the neighbours z of y in R of
+// popc(R[y] & R[z]). A warp takes a row and its lanes one neighbour z each,
+// with the same word loop on every lane, so the cost follows the edges of R
+// and not the (much larger) number of K4s of dense hub neighbourhoods.
 #include "kernels.h"
 
 namespace niorca {
