@@ -16,9 +16,10 @@ components), so every result is identical alone and in the mix.
 from __future__ import annotations
 
 import collections
+import os
 import threading
 import time
-from concurrent.futures import Future
+from concurrent.futures import Future, ThreadPoolExecutor
 
 import numpy as np
 import torch
@@ -76,7 +77,13 @@ class _Batch:
 
 
 class Server:
-    """Continuous batching over `streams` CUDA streams within `mem_budget` bytes."""
+    """Continuous batching over `streams` CUDA streams within `mem_budget` bytes.
+
+    A request's result is an int64 [n, 15] view of a page-locked buffer
+    shared by its batch (kept alive by the views).
+    """
+
+    PARALLEL_PACK_ENTRIES = 1 << 22   # batches from this many CSR entries pack on several threads
 
     def __init__(self, device: int | torch.device = 0, mem_budget: int = 8 << 30, streams: int = 3,
                  max_batch_graphs: int = 4096, max_batch_edges: int = 64 << 20):
@@ -94,6 +101,8 @@ class Server:
         self._stop = False
         self.completed = 0
         self.batches = 0
+        self._pool = ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1)),
+                                        thread_name_prefix="niorca-pack")
         self._thread = threading.Thread(target=self._loop, name="niorca-server", daemon=True)
         self._thread.start()
 
@@ -118,6 +127,7 @@ class Server:
             self._cv.notify()
         if wait:
             self._thread.join()
+            self._pool.shutdown(wait=True)
 
     def __enter__(self):
         return self
@@ -155,11 +165,26 @@ class Server:
         rowptr = slot.host("rowptr", total_n + 1, torch.int32)
         colidx = slot.host("colidx", max(total_m, 1), torch.int32)
         offs = slot.host("offs", 2 * (len(reqs) + 1), torch.int64)
-        host_out = slot.host("out", total_n * 15, torch.int64).view(total_n, 15)
+        # the counts land in a pinned buffer of their own (torch recycles
+        # those), and each request receives a view of its rows: no copy
+        host_out = torch.empty((total_n, 15), dtype=torch.int64, pin_memory=True)
         rp, ci = rowptr.numpy(), colidx.numpy()
-        for g, r in enumerate(reqs):
-            np.add(r.rowptr[:-1], np.int32(eo[g]), out=rp[vo[g]:vo[g + 1]])
-            ci[eo[g]:eo[g + 1]] = r.colidx
+
+        def pack(lo, hi):
+            for g in range(lo, hi):
+                r = reqs[g]
+                np.add(r.rowptr[:-1], np.int32(eo[g]), out=rp[vo[g]:vo[g + 1]])
+                ci[eo[g]:eo[g + 1]] = r.colidx
+
+        if total_m >= self.PARALLEL_PACK_ENTRIES and len(reqs) > 1:
+            # split the requests into runs of about equal size; numpy copies
+            # release the interpreter lock, so the runs pack in parallel
+            parts = self._pool._max_workers
+            cuts = np.searchsorted(eo, np.linspace(0, total_m, parts + 1)[1:-1])
+            bounds = [0, *sorted(set(int(c) for c in cuts) - {0, len(reqs)}), len(reqs)]
+            list(self._pool.map(lambda ab: pack(*ab), zip(bounds[:-1], bounds[1:])))
+        else:
+            pack(0, len(reqs))
         rp[-1] = total_m
         offs.numpy()[:] = np.concatenate([vo, eo])
         with torch.cuda.stream(stream):
@@ -189,7 +214,7 @@ class Server:
             if err is not None:
                 r.future.set_exception(err)
             else:
-                r.future.set_result(res[vo[g]:vo[g + 1]].copy())
+                r.future.set_result(res[vo[g]:vo[g + 1]])
         self.completed += len(b.reqs)
         self._in_use -= b.nbytes
         self._free_slots.append(b.slot)
