@@ -79,11 +79,11 @@ class _Batch:
 class Server:
     """Continuous batching over `streams` CUDA streams within `mem_budget` bytes.
 
-    A request's result is an int64 [n, 15] view of a page-locked buffer
-    shared by its batch (kept alive by the views).
+    Large batches pack their CSR and copy out their counts on a small
+    thread pool.
     """
 
-    PARALLEL_PACK_ENTRIES = 1 << 22   # batches from this many CSR entries pack on several threads
+    PARALLEL_ENTRIES = 1 << 22   # CSR entries (or count words) from which a batch uses the pool
 
     def __init__(self, device: int | torch.device = 0, mem_budget: int = 8 << 30, streams: int = 3,
                  max_batch_graphs: int = 4096, max_batch_edges: int = 64 << 20):
@@ -165,9 +165,7 @@ class Server:
         rowptr = slot.host("rowptr", total_n + 1, torch.int32)
         colidx = slot.host("colidx", max(total_m, 1), torch.int32)
         offs = slot.host("offs", 2 * (len(reqs) + 1), torch.int64)
-        # the counts land in a pinned buffer of their own (torch recycles
-        # those), and each request receives a view of its rows: no copy
-        host_out = torch.empty((total_n, 15), dtype=torch.int64, pin_memory=True)
+        host_out = slot.host("out", total_n * 15, torch.int64).view(total_n, 15)
         rp, ci = rowptr.numpy(), colidx.numpy()
 
         def pack(lo, hi):
@@ -176,15 +174,7 @@ class Server:
                 np.add(r.rowptr[:-1], np.int32(eo[g]), out=rp[vo[g]:vo[g + 1]])
                 ci[eo[g]:eo[g + 1]] = r.colidx
 
-        if total_m >= self.PARALLEL_PACK_ENTRIES and len(reqs) > 1:
-            # split the requests into runs of about equal size; numpy copies
-            # release the interpreter lock, so the runs pack in parallel
-            parts = self._pool._max_workers
-            cuts = np.searchsorted(eo, np.linspace(0, total_m, parts + 1)[1:-1])
-            bounds = [0, *sorted(set(int(c) for c in cuts) - {0, len(reqs)}), len(reqs)]
-            list(self._pool.map(lambda ab: pack(*ab), zip(bounds[:-1], bounds[1:])))
-        else:
-            pack(0, len(reqs))
+        self._runs(pack, eo)
         rp[-1] = total_m
         offs.numpy()[:] = np.concatenate([vo, eo])
         with torch.cuda.stream(stream):
@@ -201,6 +191,20 @@ class Server:
         self._inflight.append(b)
         self.batches += 1
 
+    def _runs(self, fn, offsets):
+        """fn(lo, hi) over the requests of a batch; a batch with many entries
+        (offsets: their prefix sums) is cut into runs of about equal size
+        that run on the thread pool (numpy copies release the interpreter
+        lock)."""
+        count, total = len(offsets) - 1, int(offsets[-1])
+        if total < self.PARALLEL_ENTRIES or count < 2:
+            fn(0, count)
+            return
+        parts = self._pool._max_workers
+        cuts = np.searchsorted(offsets, np.linspace(0, total, parts + 1)[1:-1])
+        bounds = [0, *sorted(set(int(c) for c in cuts) - {0, count}), count]
+        list(self._pool.map(lambda ab: fn(*ab), zip(bounds[:-1], bounds[1:])))
+
     def _retire(self, b: _Batch, now: float):
         vo = b.keep[-1]
         err = None
@@ -209,12 +213,20 @@ class Server:
         except _lib.NiorcaError as e:
             err = e
         res = b.host_out.numpy()
+        if err is None:
+            outs = [None] * len(b.reqs)
+
+            def unpack(lo, hi):
+                for g in range(lo, hi):
+                    outs[g] = res[vo[g]:vo[g + 1]].copy()
+
+            self._runs(unpack, vo * 15)
         for g, r in enumerate(b.reqs):
             r.t_done = now
             if err is not None:
                 r.future.set_exception(err)
             else:
-                r.future.set_result(res[vo[g]:vo[g + 1]])
+                r.future.set_result(outs[g])
         self.completed += len(b.reqs)
         self._in_use -= b.nbytes
         self._free_slots.append(b.slot)
