@@ -79,11 +79,11 @@ class _Batch:
 class Server:
     """Continuous batching over `streams` CUDA streams within `mem_budget` bytes.
 
-    Large batches pack their CSR and copy out their counts on a small
-    thread pool.
+    Batches pack their CSR and copy out their counts on a small thread pool;
+    a request's result is an int64 [n, 15] view of its batch's array.
     """
 
-    PARALLEL_ENTRIES = 1 << 22   # CSR entries (or count words) from which a batch uses the pool
+    PARALLEL_ENTRIES = 1 << 19   # CSR entries (or count words) from which a batch uses the pool
 
     def __init__(self, device: int | torch.device = 0, mem_budget: int = 8 << 30, streams: int = 3,
                  max_batch_graphs: int = 4096, max_batch_edges: int = 64 << 20):
@@ -205,6 +205,16 @@ class Server:
         bounds = [0, *sorted(set(int(c) for c in cuts) - {0, count}), count]
         list(self._pool.map(lambda ab: fn(*ab), zip(bounds[:-1], bounds[1:])))
 
+    def _ranges(self, fn, count, words):
+        """fn(lo, hi) over [0, count) in equal ranges on the thread pool when
+        the batch moves many words."""
+        if words < self.PARALLEL_ENTRIES or count < 2:
+            fn(0, count)
+            return
+        parts = self._pool._max_workers
+        bounds = [count * k // parts for k in range(parts + 1)]
+        list(self._pool.map(lambda k: fn(bounds[k], bounds[k + 1]), range(parts)))
+
     def _retire(self, b: _Batch, now: float):
         vo = b.keep[-1]
         err = None
@@ -212,21 +222,23 @@ class Server:
             _lib.check(b.stream)
         except _lib.NiorcaError as e:
             err = e
-        res = b.host_out.numpy()
         if err is None:
-            outs = [None] * len(b.reqs)
+            # one array per batch, filled from the staging buffer by a copy
+            # split into equal row ranges; every request gets a view of it
+            res = b.host_out.numpy()
+            total_n = int(vo[-1])
+            out = np.empty((total_n, 15), dtype=np.int64)
 
             def unpack(lo, hi):
-                for g in range(lo, hi):
-                    outs[g] = res[vo[g]:vo[g + 1]].copy()
+                out[lo:hi] = res[lo:hi]
 
-            self._runs(unpack, vo * 15)
+            self._ranges(unpack, total_n, 15 * total_n)
         for g, r in enumerate(b.reqs):
             r.t_done = now
             if err is not None:
                 r.future.set_exception(err)
             else:
-                r.future.set_result(outs[g])
+                r.future.set_result(out[vo[g]:vo[g + 1]])
         self.completed += len(b.reqs)
         self._in_use -= b.nbytes
         self._free_slots.append(b.slot)
