@@ -108,7 +108,10 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     din = np.bincount(rd2[sel], minlength=n)
     live = (din >= 2) & (w_root >= 2)
     pack_lim = (1 << (32 - int(n - 1).bit_length())) - 2     # packed tables hold counts below this
-    warp = live & (w_root <= min(c4_warp_ub, pack_lim))
+    # the warp tier packs when the count bits reach its limit, else it uses
+    # split tables of 1024 pairs (W <= 768)
+    warp_lim = c4_warp_ub if pack_lim >= c4_warp_ub else min(c4_warp_ub, 768)
+    warp = live & (w_root <= warp_lim)
     midp = live & ~warp & (w_root <= 6144) & (w_root <= pack_lim)
     mid = live & ~warp & ~midp & (w_root <= 3072)
     cta = live & ~warp & ~midp & ~mid & (w_root <= 12288)

@@ -32,6 +32,8 @@ constexpr int CW_WARPS = 4;
 constexpr int CW_SLOTS = 2048;      // packed
 constexpr int CW_MAXW = 1536;
 constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
+constexpr int CWS_SLOTS = 1024;     // split (key, count) pairs in the same 8 KB per warp
+constexpr int CWS_MAXW = 768;
 constexpr int CM_THREADS = 128;
 constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
 constexpr int CM_MAXW = 3072;      // split; 6144 when packed
@@ -352,15 +354,20 @@ struct __align__(16) C4WarpSmem {
 
 // One warp per root with W <= maxw (<= CW_MAXW) that fits a packed table;
 // other roots are queued for the wider tiers.
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists,
-                                                           int *counters, int maxw, int cb) {
+// SPLIT: tables of CWS_SLOTS (key, count) pairs in the same space, for
+// graphs whose ids leave a packed word too few count bits.
+template <bool SPLIT>
+__device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, int *counters, int maxw, int cb) {
     __shared__ C4WarpSmem sm_all[CW_WARPS];
     C4WarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
-    PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
+    const long long warp_lim = SPLIT ? (maxw < CWS_MAXW ? maxw : CWS_MAXW) : (maxw < pack_lim ? maxw : pack_lim);
+    int *const sk = reinterpret_cast<int *>(S.t), *const sc = sk + CWS_SLOTS;   // split keys, counts
+    if (SPLIT) SplitTab{sk, sc, CWS_SLOTS - 1, nullptr}.clear_all(lane, 32);
+    else PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
     __syncwarp();
     // Software pipeline over the warp's roots u, u + nw, u + 2 nw: row bounds
     // are loaded two roots ahead, the first 32 in-neighbours and their row
@@ -400,7 +407,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
             rv1 = v1 >= 0 ? g.rinfo[v1] : Z;   // next root's in-neighbours, during this walk
             rv1_loaded = true;
             if (W < 2) return;
-            if (W > maxw || W > pack_lim) {
+            if (W > warp_lim) {
                 if (lane == 0) {
                     int which, list;   // queue counter and list slot (lists + list * n)
                     if (W > CC_MAXW) { which = CNT_C4_TEAM; list = 4; }
@@ -411,11 +418,17 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
                 }
                 return;
             }
-            // at least 2W slots (W <= CW_SLOTS / 2), else the whole table (W <= 3/4 of it)
+            // at least 2W slots (W <= half the table), else the whole table (W <= 3/4 of it)
+            constexpr unsigned TS = SPLIT ? CWS_SLOTS : CW_SLOTS;
             unsigned slots = next_pow2(2 * (unsigned)W);
-            slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > CW_SLOTS ? CW_SLOTS : slots);
-            const PackedTab T{S.t, slots - 1, cb, nullptr};
-            c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
+            slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > TS ? TS : slots);
+            if constexpr (SPLIT) {
+                const SplitTab T{sk, sc, slots - 1, nullptr};
+                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
+            } else {
+                const PackedTab T{S.t, slots - 1, cb, nullptr};
+                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
+            }
         }();
         if (!rv1_loaded) rv1 = v1 >= 0 ? g.rinfo[v1] : Z;
         ru = ru1;
@@ -423,6 +436,16 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, 
         v0 = v1;
         rv0 = rv1;
     }
+}
+
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters, int maxw,
+                                                           int cb) {
+    c4_warp_body<false>(g, vacc, lists, counters, maxw, cb);
+}
+
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_split(Graph g, VAcc *vacc, int *lists, int *counters,
+                                                                 int maxw, int cb) {
+    c4_warp_body<true>(g, vacc, lists, counters, maxw, cb);
 }
 
 // Roots from a queue, one CTA each. The table (SLOTS split slots, or
@@ -651,8 +674,15 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
     const int cb = packed_count_bits(w.n);
-    k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
-                                                                         cb);
+    // a packed word holds counts up to 2^cb - 2; with many vertices (large
+    // graphs, batches) that is below what the warp tier takes, and the warp
+    // tier counts in split tables instead
+    if ((1ll << cb) - 2 >= maxw)
+        k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
+                                                                             cb);
+    else
+        k_c4_warp_split<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters,
+                                                                                   maxw, cb);
     after_launch(st, K_C4_WARP);
     k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MIDP);
