@@ -84,28 +84,43 @@ __device__ __forceinline__ int wedge_chunk(const Graph &g, int u, int b, int din
     return seg_build(T, st, len, pre);
 }
 
-// Walks the wedges of root u (in-neighbours b .. b + din of row u) in the
-// calling warp, chunk by chunk of 32 in-neighbours: f(act, q, w) on every
-// lane, act meaning that w is a wedge end through the v owned by lane
-// q; then done(v) per chunk.
-// A root with at most 32 in-neighbours has one chunk; its table may be
-// built already (built = true: T holds it, v/len/pre/total are the lane's).
-struct Chunk0 {
-    bool built;
-    int v, len, pre, total;
+// Wedge segments of a root's first two chunks of in-neighbours, held in
+// registers by the warp (lane p: in-neighbours p and 32 + p) so that its
+// walks search no row again. With one chunk (din <= 32) its segment table
+// may be built already (built0: pre0 and total0 are the lane's).
+struct RootChunks {
+    int have = 0;          // chunks held: 0, 1 or 2 (warp-uniform)
+    bool built0 = false;   // the warp's segment table holds chunk 0
+    int v0 = -1, st0 = 0, len0 = 0, v1 = -1, st1 = 0, len1 = 0;
+    int pre0 = 0, total0 = 0;
 };
 
+// Segment table of chunk c (in-neighbours 32c ...) of root u, from the
+// registers of rc when it holds the chunk, else by searching the rows.
+__device__ __forceinline__ int root_chunk(const Graph &g, int u, int b, int din, int c, SegTab &T,
+                                          const RootChunks &rc, int &v, int &len, int &pre) {
+    if (c == 0 && rc.built0) {
+        v = rc.v0, len = rc.len0, pre = rc.pre0;
+        return rc.total0;
+    }
+    if (c < rc.have) {
+        v = c == 0 ? rc.v0 : rc.v1;
+        len = c == 0 ? rc.len0 : rc.len1;
+        return seg_build(T, c == 0 ? rc.st0 : rc.st1, len, pre);
+    }
+    return wedge_chunk(g, u, b, din, 32 * c, T, v, len, pre);
+}
+
+// Walks the wedges of root u (in-neighbours b .. b + din of row u) in the
+// calling warp, chunk by chunk of 32 in-neighbours: f(act, q, w) on every
+// lane, act meaning that w is a wedge end through the v owned by lane q;
+// then done(v) per chunk.
 template <class F, class D>
 __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int din, SegTab &T, F f, D done,
-                                            Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
-    for (int cb = 0; cb < din; cb += 32) {
-        int v, len, pre, total;
-        if (c0pre.built) {
-            v = c0pre.v, len = c0pre.len, pre = c0pre.pre, total = c0pre.total;
-            c0pre.built = false;
-        } else {
-            total = wedge_chunk(g, u, b, din, cb, T, v, len, pre);
-        }
+                                            const RootChunks &rc) {
+    for (int c = 0; 32 * c < din; ++c) {
+        int v, len, pre;
+        const int total = root_chunk(g, u, b, din, c, T, rc, v, len, pre);
         seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
         __syncwarp();
         done(v);
@@ -232,7 +247,7 @@ struct PackedTab {
 template <bool CTA, class Tab>
 __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din,
                                         const Tab &T, int wid, int nw, int tid, int nthreads, SegTab &seg,
-                                        long long *pv, int *flags, Chunk0 c0pre = Chunk0{false, 0, 0, 0, 0}) {
+                                        long long *pv, int *flags, const RootChunks &rc = RootChunks{}) {
     const int lane = lane_id();
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
@@ -257,7 +272,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         }
     };
     if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
-    else walk_wedges(g, u, b, din, seg, insert, [](int) {}, c0pre);
+    else walk_wedges(g, u, b, din, seg, insert, [](int) {}, rc);
     sync();
     const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
     bool sweep = CTA ? flags[1] != 0 : false;
@@ -291,8 +306,8 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
             for (int k = 0; k < nd; ++k) {
                 const int w = flags[k], c = flags[CW_DUPS + k];
                 const int4 rw = g.rinfo[w];
-                for (int p = lane; p < din; p += 32) {
-                    const int v = g.ncol[b + p];
+                for (int ch = 0, p = lane; p < din; ++ch, p += 32) {
+                    const int v = ch < rc.have ? (ch == 0 ? rc.v0 : rc.v1) : g.ncol[b + p];
                     if (find_sorted(g.ncol, rw.x, rw.z, v) >= 0) add64(&vacc[v].C4, c - 1);
                 }
             }
@@ -327,7 +342,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
             pv[lane] = 0;
         };
         if (CTA) walk_wedges_cta<true>(g, u, b, din, wid, nw, seg, middle, flush);
-        else walk_wedges(g, u, b, din, seg, middle, flush);
+        else walk_wedges(g, u, b, din, seg, middle, flush, rc);
         sync();
     }
     if (CTA) {
@@ -388,18 +403,28 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
             const int b = ru.x, din = ru.y - ru.x;
             if (din < 2) return;
             long long W = 0;   // exact wedge count W of root u
-            Chunk0 c0pre{false, 0, 0, 0, 0};
-            if (din <= 32) {   // one chunk: its segment table gives W
-                int st = 0, len = 0;
+            RootChunks rc;
+            if (din <= 64) {   // both chunks' segments stay in registers
+                rc.v0 = v0;
                 if (lane < din) {
-                    st = rv0.x;
-                    len = wedge_len(g, u, rv0);
+                    rc.st0 = rv0.x;
+                    rc.len0 = wedge_len(g, u, rv0);
                 }
-                c0pre.v = v0;
-                c0pre.len = len;
-                c0pre.total = seg_build(S.seg, st, len, c0pre.pre);
-                c0pre.built = true;
-                W = c0pre.total;
+                if (din <= 32) {   // one chunk: its segment table gives W
+                    rc.have = 1;
+                    rc.total0 = seg_build(S.seg, rc.st0, rc.len0, rc.pre0);
+                    rc.built0 = true;
+                    W = rc.total0;
+                } else {
+                    rc.have = 2;
+                    if (32 + lane < din) {
+                        rc.v1 = g.ncol[b + 32 + lane];
+                        const int4 r1 = g.rinfo[rc.v1];
+                        rc.st1 = r1.x;
+                        rc.len1 = wedge_len(g, u, r1);
+                    }
+                    W = warp_sum(rc.len0 + rc.len1);
+                }
             } else {
                 for (int p = lane; p < din; p += 32) W += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
                 W = warp_sum(W);
@@ -424,10 +449,10 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
             slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > TS ? TS : slots);
             if constexpr (SPLIT) {
                 const SplitTab T{sk, sc, slots - 1, nullptr};
-                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
+                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc);
             } else {
                 const PackedTab T{S.t, slots - 1, cb, nullptr};
-                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, c0pre);
+                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc);
             }
         }();
         if (!rv1_loaded) rv1 = v1 >= 0 ? g.rinfo[v1] : Z;
