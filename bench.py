@@ -76,10 +76,11 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     B_c4  = 4 * number of wedges u - v - w with v, w below u (cycle roots)
     B_csr = 4 (n + 1) + 4 m, B_out = 120 n.
     A root's wedges (or triangle probes) count for the tier kernel that
-    takes it: 4-cycle roots by their wedge count W (warp <= 1536 with a
-    packed table, packed mid <= 6144, split mid <= 3072, cta <= 12288, else
-    global), triangle roots by out-degree (warp <= 64, cta <= 256, else
-    big).
+    takes it: 4-cycle roots by their wedge count W (with packed tables warp
+    <= 1152 and warp_big <= 1536, with split tables warp <= 576 and
+    warp_big <= 768; then packed mid <= 6144, split mid <= 3072, cta <=
+    12288, else global), triangle roots by out-degree (warp <= 64, cta <=
+    256, else big).
     """
     n = len(rowptr) - 1
     m = len(colidx)
@@ -108,15 +109,20 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
     din = np.bincount(rd2[sel], minlength=n)
     live = (din >= 2) & (w_root >= 2)
     pack_lim = (1 << (32 - int(n - 1).bit_length())) - 2     # packed tables hold counts below this
-    # the warp tier packs when the count bits reach its limit, else it uses
-    # split tables of 1024 pairs (W <= 768)
-    warp_lim = c4_warp_ub if pack_lim >= c4_warp_ub else min(c4_warp_ub, 768)
+    # the warp tiers pack when the count bits reach their limit, else they
+    # use split tables of half as many slots; each takes W up to 3/4 of its
+    # slots (k_c4_warp 1536 words, k_c4_warp_big 2048)
+    packed = pack_lim >= c4_warp_ub
+    warp_lim = min(c4_warp_ub, 1152 if packed else 576)
+    big_lim = min(c4_warp_ub, 1536 if packed else 768)
     warp = live & (w_root <= warp_lim)
-    midp = live & ~warp & (w_root <= 6144) & (w_root <= pack_lim)
-    mid = live & ~warp & ~midp & (w_root <= 3072)
-    cta = live & ~warp & ~midp & ~mid & (w_root <= 12288)
-    tiers = {"k_c4_warp": warp, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
-             "k_c4_team": live & (w_root > 12288)}
+    wbig = live & ~warp & (w_root <= big_lim)
+    rest = live & ~warp & ~wbig
+    midp = rest & (w_root <= 6144) & (w_root <= pack_lim)
+    mid = rest & ~midp & (w_root <= 3072)
+    cta = rest & ~midp & ~mid & (w_root <= 12288)
+    tiers = {"k_c4_warp": warp, "k_c4_warp_big": wbig, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
+             "k_c4_team": rest & (w_root > 12288)}
     w_c4 = int(w_root.sum())
     # B_k4 = 4 * sum over oriented edges (u, v) and w in S = N+(u) ∩ N+(v) of
     # min(d+w, |S|): the probes for the edges inside each common out-

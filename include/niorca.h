@@ -203,7 +203,7 @@ int32_t niorca_version(void);
  * OpenMP schedules and chunk sizes, Sec. 8). values[i] for i < count sets,
  * for the current device and every later call on it:
  *   0..4  CTAs per SM of the relabel, triangle, edge-aggregate, 4-cycle and
- *         solve kernels (1..64; defaults 16, 8, 8, 6, 8)
+ *         solve kernels (1..64; defaults 16, 8, 8, 8, 8)
  *   5     degree class from which a row is relabelled by a whole CTA
  *         (1..127; default 32, i.e. degree >= 512)
  *   6     largest wedge count W of a 4-cycle root handled by one warp (2..1536)

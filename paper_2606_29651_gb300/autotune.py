@@ -22,13 +22,13 @@ import torch
 from . import _lib
 
 SEARCH = {
-    "grid_c4": (3, 6, 12, 18),
+    "grid_c4": (4, 8, 16),
     "grid_tri": (2, 4, 8, 16),
     "grid_relabel": (4, 8, 16),
     "grid_agg": (4, 8, 16),
     "grid_solve": (4, 8, 16),
     "warp_maxd": (32, 64),
-    "c4_warp_maxw": (512, 1024, 1536),
+    "c4_warp_maxw": (768, 1152, 1536),
     "long_row_class": (24, 28, 32, 36),   # rows of degree >= 128, 256, 512, 1024 get a CTA
 }
 

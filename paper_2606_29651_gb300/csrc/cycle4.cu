@@ -29,11 +29,12 @@
 namespace niorca {
 
 constexpr int CW_WARPS = 4;
-constexpr int CW_SLOTS = 2048;      // packed
-constexpr int CW_MAXW = 1536;
+constexpr int CW_WORDS = 1536;      // table words per warp of k_c4_warp: 6 KB, 8 CTAs of 4 warps per SM
+constexpr int CWB_WORDS = 2048;     // k_c4_warp_big: 8 KB, 6 CTAs per SM
+constexpr int CW_MAXW = 1536;       // largest W of a root in the warp tiers
 constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
-constexpr int CWS_SLOTS = 1024;     // split (key, count) pairs in the same 8 KB per warp
-constexpr int CWS_MAXW = 768;
+constexpr int CW_BIG_LIST = 0;      // list slot of k_c4_warp_big's roots: the triangle stage's heavy list,
+                                    // which nothing reads after that stage
 constexpr int CM_THREADS = 128;
 constexpr int CM_SLOTS = 4096;      // split; 8192 when packed
 constexpr int CM_MAXW = 3072;      // split; 6144 when packed
@@ -148,41 +149,42 @@ __device__ __forceinline__ void walk_wedges_cta(const Graph &g, int u, int b, in
     }
 }
 
-// Probe sequence of the 4-cycle count tables (mask + 1 = 2^k slots): first
-// the top k bits of the key times 2^32 / golden ratio (Fibonacci hashing),
-// then the top bits of a second multiplicative hash, then linear from there.
-// Keys whose first slots collide part ways at the second probe, which keeps
-// the runs, and so a warp's slowest insert, short.
-__device__ __forceinline__ unsigned fib_slot(int key, unsigned mask) {
-    return (static_cast<unsigned>(key) * 0x9E3779B1u) >> (__clz(mask + 1) + 1);
+// Probe sequence of the 4-cycle count tables (any size S): first the high
+// word of S times the key times 2^32 / golden ratio (Fibonacci hashing; for
+// S = 2^k the top k bits of the product), then the same with a second
+// multiplier, then linear from there. Keys whose first slots collide part
+// ways at the second probe, which keeps the runs, and so a warp's slowest
+// insert, short.
+__device__ __forceinline__ unsigned fib_slot(int key, unsigned size) {
+    return __umulhi(static_cast<unsigned>(key) * 0x9E3779B1u, size);
 }
-__device__ __forceinline__ unsigned next_probe(unsigned s, unsigned probe, int key, unsigned mask) {
-    return probe == 0 ? (static_cast<unsigned>(key) * 0x85EBCA77u) >> (__clz(mask + 1) + 1) : (s + 1) & mask;
+__device__ __forceinline__ unsigned next_probe(unsigned s, unsigned probe, int key, unsigned size) {
+    return probe == 0 ? __umulhi(static_cast<unsigned>(key) * 0x85EBCA77u, size) : (s + 1 == size ? 0u : s + 1);
 }
 
-// Split table: keys (-1 empty) and counts in two arrays.
+// Split table of `size` slots: keys (-1 empty) and counts in two arrays.
 struct SplitTab {
     int *hk, *hc;
-    unsigned mask;
+    unsigned size;
     unsigned short *touched;   // slots filled (CTA groups)
     // counts w; returns the slot if this call inserted w, -1 if w was there
     __device__ __forceinline__ int add(int w) const {
-        unsigned s = fib_slot(w, mask);
-        for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned s = fib_slot(w, size);
+        for (unsigned probe = 0; probe < size; ++probe) {
             const int prev = atomicCAS(&hk[s], -1, w);
             if (prev == -1) { atomicAdd(&hc[s], 1); return (int)s; }
             if (prev == w) { atomicAdd(&hc[s], 1); return -1; }
-            s = next_probe(s, probe, w, mask);
+            s = next_probe(s, probe, w, size);
         }
         return -1;
     }
     __device__ __forceinline__ int get(int w) const {
-        unsigned s = fib_slot(w, mask);
-        for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned s = fib_slot(w, size);
+        for (unsigned probe = 0; probe < size; ++probe) {
             const int k = hk[s];
             if (k == w) return hc[s];
             if (k == -1) return 0;
-            s = next_probe(s, probe, w, mask);
+            s = next_probe(s, probe, w, size);
         }
         return 0;
     }
@@ -191,37 +193,37 @@ struct SplitTab {
     __device__ __forceinline__ int cnt(int s) const { return hc[s]; }
     __device__ __forceinline__ void clear(int s) const { hk[s] = -1; hc[s] = 0; }
     __device__ __forceinline__ void clear_all(int tid, int nthreads) const {
-        for (int i = tid; i <= (int)mask; i += nthreads) { hk[i] = -1; hc[i] = 0; }
+        for (int i = tid; i < (int)size; i += nthreads) { hk[i] = -1; hc[i] = 0; }
     }
 };
 
-// Packed table: one word (w << cb) | count per slot, EMPTY when free. A
-// count never reaches 2^cb - 1 (the caller ensures W < 2^cb - 1), so a full
-// word is never EMPTY.
+// Packed table of `size` slots (a multiple of 4): one word (w << cb) |
+// count per slot, EMPTY when free. A count never reaches 2^cb - 1 (the
+// caller ensures W < 2^cb - 1), so a full word is never EMPTY.
 struct PackedTab {
     unsigned *t;
-    unsigned mask;
+    unsigned size;
     int cb;
     unsigned short *touched;   // slots filled (CTA groups)
     __device__ __forceinline__ int add(int w) const {
         const unsigned key = static_cast<unsigned>(w);
-        unsigned s = fib_slot(w, mask);
-        for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned s = fib_slot(w, size);
+        for (unsigned probe = 0; probe < size; ++probe) {
             const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
             if (prev == EMPTY) return (int)s;
             if ((prev >> cb) == key) { atomicAdd(&t[s], 1u); return -1; }
-            s = next_probe(s, probe, w, mask);
+            s = next_probe(s, probe, w, size);
         }
         return -1;
     }
     __device__ __forceinline__ int get(int w) const {
         const unsigned key = static_cast<unsigned>(w);
-        unsigned s = fib_slot(w, mask);
-        for (unsigned probe = 0; probe <= mask; ++probe) {
+        unsigned s = fib_slot(w, size);
+        for (unsigned probe = 0; probe < size; ++probe) {
             const unsigned cur = t[s];
             if (cur == EMPTY) return 0;
             if ((cur >> cb) == key) return (int)(cur & ((1u << cb) - 1));
-            s = next_probe(s, probe, w, mask);
+            s = next_probe(s, probe, w, size);
         }
         return 0;
     }
@@ -231,7 +233,7 @@ struct PackedTab {
     __device__ __forceinline__ void clear(int s) const { t[s] = EMPTY; }
     __device__ __forceinline__ void clear_all(int tid, int nthreads) const {
         uint4 *t4 = reinterpret_cast<uint4 *>(t);
-        for (int i = tid; i < (int)(mask + 1) / 4; i += nthreads) t4[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
+        for (int i = tid; i < (int)size / 4; i += nthreads) t4[i] = make_uint4(EMPTY, EMPTY, EMPTY, EMPTY);
     }
 };
 
@@ -274,7 +276,7 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     if (CTA) walk_wedges_cta<false>(g, u, b, din, wid, nw, seg, insert, [](int) {});
     else walk_wedges(g, u, b, din, seg, insert, [](int) {}, rc);
     sync();
-    const int nt = CTA ? flags[0] : (int)T.mask + 1;   // entries of the list, or slots swept
+    const int nt = CTA ? flags[0] : (int)T.size;   // entries of the list, or slots swept
     bool sweep = CTA ? flags[1] != 0 : false;
     if (!CTA && __any_sync(FULL, dup_l)) {
         // A warp sweeps its table for the repeated keys (count >= 2), credits
@@ -360,43 +362,60 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
 
 constexpr int CW_MIN_SLOTS = 64;
 
+template <int WORDS>
 struct __align__(16) C4WarpSmem {
-    unsigned t[CW_SLOTS];
+    unsigned t[WORDS];
     SegTab seg;
     long long pv[32];
     int dups[2 * CW_DUPS];   // repeated keys of a root and their counts
 };
 
-// One warp per root with W <= maxw (<= CW_MAXW) that fits a packed table;
-// other roots are queued for the wider tiers.
-// SPLIT: tables of CWS_SLOTS (key, count) pairs in the same space, for
-// graphs whose ids leave a packed word too few count bits.
-template <bool SPLIT>
+// Slots of a warp's table of WORDS words (packed words, or split (key,
+// count) pairs), and the largest W it takes: 3/4 of the slots.
+__host__ __device__ constexpr int cw_slots(bool split, int words) { return split ? words / 2 : words; }
+__host__ __device__ constexpr int cw_maxw(bool split, int words) { return cw_slots(split, words) / 4 * 3; }
+
+// One warp per root. k_c4_warp (BIG = false) takes every vertex as a root:
+// those with W up to 3/4 of its 6 KB table are counted there, those that
+// fit the 8 KB table of k_c4_warp_big (BIG = true) are queued for it, the
+// rest for the wider tiers. SPLIT: (key, count) pair tables, for graphs
+// whose ids leave a packed word too few count bits.
+template <bool SPLIT, bool BIG>
 __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, int *counters, int maxw, int cb) {
-    __shared__ C4WarpSmem sm_all[CW_WARPS];
-    C4WarpSmem &S = sm_all[threadIdx.x >> 5];
+    constexpr int WORDS = BIG ? CWB_WORDS : CW_WORDS;
+    constexpr int TS = cw_slots(SPLIT, WORDS);
+    __shared__ C4WarpSmem<WORDS> sm_all[CW_WARPS];
+    C4WarpSmem<WORDS> &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     const long long pack_lim = (1ll << cb) - 2;   // largest W a packed count may reach
-    const long long warp_lim = SPLIT ? (maxw < CWS_MAXW ? maxw : CWS_MAXW) : (maxw < pack_lim ? maxw : pack_lim);
-    int *const sk = reinterpret_cast<int *>(S.t), *const sc = sk + CWS_SLOTS;   // split keys, counts
-    if (SPLIT) SplitTab{sk, sc, CWS_SLOTS - 1, nullptr}.clear_all(lane, 32);
-    else PackedTab{S.t, CW_SLOTS - 1, cb, nullptr}.clear_all(lane, 32);
+    const long long warp_cap = SPLIT ? maxw : (maxw < pack_lim ? maxw : pack_lim);   // W the warp tiers take
+    const long long here_lim = warp_cap < cw_maxw(SPLIT, WORDS) ? warp_cap : cw_maxw(SPLIT, WORDS);
+    const long long big_lim = warp_cap < cw_maxw(SPLIT, CWB_WORDS) ? warp_cap : cw_maxw(SPLIT, CWB_WORDS);
+    int *const big_roots = lists + (size_t)CW_BIG_LIST * g.n;
+    const int count = BIG ? counters[CNT_C4_WBIG] : g.n;
+    auto root = [&](int i) { return BIG ? big_roots[i] : i; };
+    int *const sk = reinterpret_cast<int *>(S.t), *const sc = sk + TS;   // split keys, counts
+    if (SPLIT) SplitTab{sk, sc, (unsigned)TS, nullptr}.clear_all(lane, 32);
+    else PackedTab{S.t, (unsigned)TS, cb, nullptr}.clear_all(lane, 32);
     __syncwarp();
-    // Software pipeline over the warp's roots u, u + nw, u + 2 nw: row bounds
+    // Software pipeline over the warp's roots i, i + nw, i + 2 nw: row bounds
     // are loaded two roots ahead, the first 32 in-neighbours and their row
     // bounds one root ahead, so that a root starts with its data in flight.
     const int4 Z = make_int4(0, 0, 0, 0);
-    int u = gw;
-    int4 ru = u < g.n ? g.rinfo[u] : Z;
-    int4 ru1 = u + nw < g.n ? g.rinfo[u + nw] : Z;
-    int v0 = (u < g.n && lane < ru.y - ru.x) ? g.ncol[ru.x + lane] : -1;
+    int i = gw;
+    int u = i < count ? root(i) : 0;
+    int un = i + nw < count ? root(i + nw) : 0;
+    int4 ru = i < count ? g.rinfo[u] : Z;
+    int4 ru1 = i + nw < count ? g.rinfo[un] : Z;
+    int v0 = (i < count && lane < ru.y - ru.x) ? g.ncol[ru.x + lane] : -1;
     int4 rv0 = v0 >= 0 ? g.rinfo[v0] : Z;
-    for (; u < g.n; u += nw) {
-        const int u2 = u + 2 * nw;
-        const int4 ru2 = u2 < g.n ? g.rinfo[u2] : Z;
-        const int v1 = (u + nw < g.n && lane < ru1.y - ru1.x) ? g.ncol[ru1.x + lane] : -1;
+    for (; i < count; i += nw) {
+        const int i2 = i + 2 * nw;
+        const int u2 = i2 < count ? root(i2) : 0;
+        const int4 ru2 = i2 < count ? g.rinfo[u2] : Z;
+        const int v1 = (i + nw < count && lane < ru1.y - ru1.x) ? g.ncol[ru1.x + lane] : -1;
         int4 rv1 = Z;
         bool rv1_loaded = false;
         [&] {
@@ -432,10 +451,11 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
             rv1 = v1 >= 0 ? g.rinfo[v1] : Z;   // next root's in-neighbours, during this walk
             rv1_loaded = true;
             if (W < 2) return;
-            if (W > warp_lim) {
+            if (W > here_lim) {
                 if (lane == 0) {
                     int which, list;   // queue counter and list slot (lists + list * n)
-                    if (W > CC_MAXW) { which = CNT_C4_TEAM; list = 4; }
+                    if (!BIG && W <= big_lim) { which = CNT_C4_WBIG; list = CW_BIG_LIST; }
+                    else if (W > CC_MAXW) { which = CNT_C4_TEAM; list = 4; }
                     else if (W <= 2 * CM_MAXW && W <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
                     else if (W <= CM_MAXW) { which = CNT_C4_MID; list = 2; }
                     else { which = CNT_C4_CTA; list = 3; }
@@ -444,18 +464,19 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
                 return;
             }
             // at least 2W slots (W <= half the table), else the whole table (W <= 3/4 of it)
-            constexpr unsigned TS = SPLIT ? CWS_SLOTS : CW_SLOTS;
             unsigned slots = next_pow2(2 * (unsigned)W);
-            slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > TS ? TS : slots);
+            slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > (unsigned)TS ? (unsigned)TS : slots);
             if constexpr (SPLIT) {
-                const SplitTab T{sk, sc, slots - 1, nullptr};
+                const SplitTab T{sk, sc, slots, nullptr};
                 c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc);
             } else {
-                const PackedTab T{S.t, slots - 1, cb, nullptr};
+                const PackedTab T{S.t, slots, cb, nullptr};
                 c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc);
             }
         }();
         if (!rv1_loaded) rv1 = v1 >= 0 ? g.rinfo[v1] : Z;
+        u = un;
+        un = u2;
         ru = ru1;
         ru1 = ru2;
         v0 = v1;
@@ -463,14 +484,25 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
     }
 }
 
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters, int maxw,
-                                                           int cb) {
-    c4_warp_body<false>(g, vacc, lists, counters, maxw, cb);
+// 8 CTAs of 4 warps per SM: 6 KB tables and at most 64 registers a thread.
+__global__ void __launch_bounds__(CW_WARPS * 32, 8) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters,
+                                                              int maxw, int cb) {
+    c4_warp_body<false, false>(g, vacc, lists, counters, maxw, cb);
 }
 
-__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_split(Graph g, VAcc *vacc, int *lists, int *counters,
-                                                                 int maxw, int cb) {
-    c4_warp_body<true>(g, vacc, lists, counters, maxw, cb);
+__global__ void __launch_bounds__(CW_WARPS * 32, 8) k_c4_warp_split(Graph g, VAcc *vacc, int *lists,
+                                                                    int *counters, int maxw, int cb) {
+    c4_warp_body<true, false>(g, vacc, lists, counters, maxw, cb);
+}
+
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_big(Graph g, VAcc *vacc, int *lists, int *counters,
+                                                               int maxw, int cb) {
+    c4_warp_body<false, true>(g, vacc, lists, counters, maxw, cb);
+}
+
+__global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_big_split(Graph g, VAcc *vacc, int *lists,
+                                                                     int *counters, int maxw, int cb) {
+    c4_warp_body<true, true>(g, vacc, lists, counters, maxw, cb);
 }
 
 // Roots from a queue, one CTA each. The table (SLOTS split slots, or
@@ -500,11 +532,10 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
         const int u = list[h];
         const int4 ru = g.rinfo[u];
         if (PACKED) {
-            const PackedTab T{words, 2 * SLOTS - 1, cb, touched};
+            const PackedTab T{words, 2 * SLOTS, cb, touched};
             c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
         } else {
-            const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS - 1,
-                             touched};
+            const SplitTab T{reinterpret_cast<int *>(words), reinterpret_cast<int *>(words + SLOTS), SLOTS, touched};
             c4_root<true>(g, vacc, u, ru.x, ru.y - ru.x, T, wid, NW, threadIdx.x, THREADS, seg, pv, flags);
         }
     }
@@ -702,13 +733,20 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     // a packed word holds counts up to 2^cb - 2; with many vertices (large
     // graphs, batches) that is below what the warp tier takes, and the warp
     // tier counts in split tables instead
-    if ((1ll << cb) - 2 >= maxw)
+    const bool packed = (1ll << cb) - 2 >= maxw;
+    if (packed)
         k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
                                                                              cb);
     else
         k_c4_warp_split<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters,
                                                                                    maxw, cb);
     after_launch(st, K_C4_WARP);
+    // roots k_c4_warp queued for the 8 KB tables: one resident wave
+    if (packed)
+        k_c4_warp_big<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb);
+    else
+        k_c4_warp_big_split<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb);
+    after_launch(st, K_C4_WARP_BIG);
     k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MIDP);
     k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
@@ -726,6 +764,11 @@ void launch_cycle4(Work &w, cudaStream_t st) {
 }
 
 void configure_cycle4() {
+    // the warp tiers need nearly all of an SM's shared memory for full residency
+    cudaFuncSetAttribute(k_c4_warp, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_c4_warp_split, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_c4_warp_big, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_c4_warp_big_split, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_midp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM);

@@ -27,7 +27,7 @@ struct Work {
     int c4slots = 0;         // rows in c4dense (each n ints), one per team of CTAs
     int *status = nullptr;   // device status word (not part of the carve)
     int num_sms = 0;
-    int tune[8] = {16, 8, 8, 6, 8, 32, 1536, 64};  // see TuneIndex
+    int tune[8] = {16, 8, 8, 8, 8, 32, 1536, 64};  // see TuneIndex
     int induced = 0;         // write induced instead of non-induced counts
 };
 
@@ -49,7 +49,7 @@ enum TuneIndex {
 // The triangle and aggregate heavy lists hold two tiers each: CTA-sized
 // roots from the front (CNT_*_HEAVY), the largest from the back (CNT_*_BIG).
 enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_TEAM = 3, CNT_DMAX = 4, CNT_C4_MID = 5,
-       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8 };
+       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8, CNT_C4_WBIG = 9 };
 
 constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
 constexpr int SCAN_TILE = 4096;      // elements per scan block
@@ -74,7 +74,7 @@ void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *st
 enum KernelId {
     K_CLASS_HIST, K_SCAN, K_CLASS_SCATTER, K_RELABEL_WARP, K_RELABEL_CTA, K_BATCH_SETUP,
     K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_ZERO, K_C4_TEAM,
-    K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_COUNT
+    K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_C4_WARP_BIG, K_COUNT
 };
 const char *kernel_name(int id);
 

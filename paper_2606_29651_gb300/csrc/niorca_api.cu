@@ -37,7 +37,8 @@ thread_local Timeline *t_cur = nullptr;
 const char *const kNames[K_COUNT] = {
     "k_class_hist", "k_scan", "k_class_scatter", "k_relabel_rows_warp", "k_relabel_rows_cta", "k_batch_setup",
     "k_tri_warp", "k_tri_cta", "k_agg_warp", "k_agg_cta", "k_c4_warp", "k_c4_cta", "k_c4_zero_dense",
-    "k_c4_team", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big"};
+    "k_c4_team", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big",
+    "k_c4_warp_big"};
 }  // namespace
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
@@ -96,7 +97,7 @@ struct DeviceState {
     cudaMemPool_t pool = nullptr;
     int *status = nullptr;
     int num_sms = 0;
-    int tune[TUNE_COUNT] = {16, 8, 8, 6, 8, 32, 1536, 64};
+    int tune[TUNE_COUNT] = {16, 8, 8, 8, 8, 32, 1536, 64};
 };
 
 constexpr int MAX_DEVICES = 64;

@@ -68,6 +68,23 @@ def test_complete_graphs_across_triangle_tiers(ni):
         assert_same(gpu_count(ni, *gg.complete(n)), np.tile(np.array(closed_complete(n)), (n, 1)), f"K{n}")
 
 
+@pytest.mark.parametrize("pad", [0, (1 << 21) + 5000 - 10000])
+def test_four_cycle_warp_tiers_both_table_kinds(ni, pad):
+    # An ER core (n = 10^4, mean degree 40) puts 4-cycle roots in both warp
+    # tiers and the 4-warp tiers above them. Isolated vertices beyond 2^21
+    # leave a packed word 10 count bits, so that every tier counts in split
+    # (key, count) tables instead of packed ones.
+    import bench
+
+    rp, ci = gg.er_mean_degree(10000, 40, 7)
+    exp = np.zeros((10000 + pad, 15), np.int64)
+    exp[:10000] = oracle.count(rp, ci)
+    rpf = np.concatenate([rp, np.full(pad, rp[-1], rp.dtype)])
+    tiers = bench.algorithmic_bytes(rpf, ci)["per_kernel"]
+    assert tiers["k_c4_warp"] > 0 and tiers["k_c4_warp_big"] > 0 and tiers["k_c4_midp"] > 0
+    assert_same(gpu_count(ni, rpf, ci), exp, f"ER core + {pad} isolated vertices")
+
+
 @pytest.mark.parametrize("name,make", [
     ("er2000", lambda: gg.er(2000, 0.01, 1)),
     ("rmat12", lambda: gg.rmat(12, 16, seed=3)),
