@@ -41,6 +41,24 @@ def test_algorithmic_bytes_small_cases():
     assert ab["W_c4"] == 3
 
 
+@pytest.mark.parametrize("pad", [0, (1 << 21) + 5000 - 3000])
+def test_four_cycle_tiers_partition_the_wedges(pad):
+    # Every live root's wedges go to exactly one 4-cycle kernel, so the
+    # per-kernel bytes add up to B_c4 (less the roots with W < 2 or fewer
+    # than two in-neighbours, which no kernel walks), with packed tables
+    # and, past 2^21 vertices, split ones.
+    rp, ci = gg.er_mean_degree(3000, 48, 5)
+    rp = np.concatenate([rp, np.full(pad, rp[-1], rp.dtype)])
+    ab = bench.algorithmic_bytes(rp, ci)
+    tiers = {k: v for k, v in ab["per_kernel"].items() if k.startswith("k_c4")}
+    assert set(tiers) == {"k_c4_warp", "k_c4_warp_big", "k_c4_midp", "k_c4_mid", "k_c4_cta", "k_c4_team"}
+    assert 0 < sum(tiers.values()) <= ab["B_c4"]
+    assert ab["B_c4"] - sum(tiers.values()) < 0.001 * ab["B_c4"]
+    assert tiers["k_c4_warp"] > 0 and tiers["k_c4_warp_big"] > 0
+    if pad:   # split tables: the warp tiers stop at W = 576 and 768
+        assert tiers["k_c4_mid"] > 0 or tiers["k_c4_midp"] > 0
+
+
 def test_deg_class_matches_library_rule():
     d = np.array([0, 1, 7, 8, 9, 10, 12, 15, 16, 20, 1 << 20, (1 << 20) + (1 << 19)])
     c = bench.deg_class(d)
