@@ -55,7 +55,7 @@ constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
 constexpr int SCAN_TILE = 4096;      // elements per scan block
 constexpr int LONG_ROW_CLASS = 32;   // deg_class(512): rows from here on get a CTA each
 // Dense rows (one per cluster of CTAs) of the largest 4-cycle tier, n ints each.
-int c4_team_rows(int num_sms);
+int c4_team_rows(int num_sms, long long n);
 inline size_t c4_dense_words(long long rows, long long n) { return (size_t)(rows * n); }
 
 size_t scan_partials(long long len);

@@ -144,7 +144,7 @@ Layout plan(long long n, long long m, int num_sms, bool batch) {
     L.ntiles = (int)((n + RL_TILE - 1) / RL_TILE);
     // the dense 4-cycle rows are only reachable by a root with more than
     // 12288 wedges, which needs m above that; one row per team of CTAs
-    L.c4slots = m > 12288 ? c4_team_rows(num_sms) : 0;
+    L.c4slots = m > 12288 ? c4_team_rows(num_sms, n) : 0;
     const long long nt = L.ntiles;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + (bytes ? bytes : 1)); return at; };
