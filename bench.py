@@ -165,7 +165,11 @@ class ClockSampler:
     def __init__(self, uuid: str | None):
         self.uuid = uuid
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the raw samples go to NIORCA_CLOCKS_DIR (default: the temp dir); the
+        # JSON line carries their summary
+        import tempfile
+        self.path = os.path.join(os.environ.get("NIORCA_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
