@@ -12,10 +12,10 @@
 //   each middle vertex v gets sum over its wedges of (c_w - 1).
 // The wedges through v are the entries of row v below u: a prefix of row v
 // ending at the position of u, which a search of N+(v) finds. Roots are
-// routed by their wedge count W (a count is at most W too): one warp
-// (k_c4_warp), four warps (k_c4_midp / k_c4_mid), a 512-thread CTA
-// (k_c4_cta), or a cluster of CTAs sharing a dense count row in global
-// memory (k_c4_team). The other tables are open-addressing hash tables in
+// routed by their wedge count W (a count is at most W too): one warp with a
+// 6 KB table (k_c4_warp) or an 8 KB one (k_c4_warp_big), four warps
+// (k_c4_midp / k_c4_mid), a 512-thread CTA (k_c4_cta), or a cluster of
+// CTAs sharing a dense count row in global memory (k_c4_team). The other tables are open-addressing hash tables in
 // shared memory, either split (key and count arrays) or packed (key << cb |
 // count in one 32-bit word, cb = 32 - bits(n - 1) count bits, usable while
 // W < 2^cb - 1), which holds twice the keys in the same space. Each table
