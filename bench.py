@@ -68,91 +68,164 @@ def deg_class(d: np.ndarray) -> np.ndarray:
     return c
 
 
-def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 1536, warp_maxd: int = 64) -> dict:
+# Routing limits of the library at its default launch shape (niorca.h,
+# niorca_set_tuning): triangle roots by out-degree, 4-cycle roots by wedges.
+TRI_WARP_MAXD, TRI_CTA_MAXD, TRI_BITS_MAXD, TRI_HASH_MAXD = 64, 256, 1152, 8192
+C4_MID_MAXW, C4_CTA_MAXW = 3072, 12288
+
+
+class Shape:
+    """The relabelled (degree-class ordered) graph as the library sees it.
+
+    order[r] = caller id of relabelled vertex r; dplus[r] = out-degree;
+    w_root[r] = wedges u - v - w with v, w below r (the 4-cycle work of root
+    r); (ou, ov) = the oriented edges, sorted by (u, v).
+    """
+
+    def __init__(self, rowptr: np.ndarray, colidx: np.ndarray):
+        n = len(rowptr) - 1
+        m = len(colidx)
+        d = np.diff(rowptr).astype(np.int64)
+        order = np.lexsort((np.arange(n), deg_class(d)))
+        rank = np.empty(n, np.int64)
+        rank[order] = np.arange(n)
+        key = np.repeat(rank * n, d)
+        key += rank[colidx.astype(np.int64)]
+        key.sort()                                  # rows by rank, each ascending
+        rs = key // n
+        rd = key - rs * n
+        del key
+        start = np.zeros(n + 1, np.int64)
+        start[1:] = np.cumsum(np.bincount(rs, minlength=n))
+        out = rd > rs
+        self.n, self.m, self.order, self.d = n, m, order, d[order]
+        self.ou, self.ov = rs[out], rd[out]
+        self.dplus = np.bincount(self.ou, minlength=n)
+        # the in-entry (v -> u), v < u, sits at position p of row v: p wedges
+        # of root u pass through v
+        pos = np.arange(m, dtype=np.int64) - start[rs]
+        del out
+        # entries (v, u) with u > v are the out-entries; wedges through v below u
+        sel = rd > rs
+        self.w_root = np.bincount(rd[sel], weights=pos[sel], minlength=n).astype(np.int64)
+        self.din = np.bincount(rd[sel], minlength=n)
+
+    def c4_tiers(self, c4_warp_ub: int = 1536) -> dict:
+        """Relabelled ids of the roots of every 4-cycle kernel."""
+        n, w = self.n, self.w_root
+        live = (self.din >= 2) & (w >= 2)
+        pack_lim = (1 << (32 - int(max(n - 1, 1)).bit_length())) - 2   # packed tables hold counts below this
+        packed = pack_lim >= c4_warp_ub
+        warp_lim = min(c4_warp_ub, 1152 if packed else 576)
+        big_lim = min(c4_warp_ub, 1536 if packed else 768)
+        warp = live & (w <= warp_lim)
+        wbig = live & ~warp & (w <= big_lim)
+        rest = live & ~warp & ~wbig
+        team = rest & (w > C4_CTA_MAXW)
+        midp = rest & ~team & (w <= 2 * C4_MID_MAXW) & (w <= pack_lim)
+        mid = rest & ~team & ~midp & (w <= C4_MID_MAXW)
+        cta = rest & ~team & ~midp & ~mid
+        return {"k_c4_warp": warp, "k_c4_warp_big": wbig, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
+                "k_c4_tiled": team}
+
+    def tri_tiers(self, warp_maxd: int = TRI_WARP_MAXD) -> dict:
+        """Relabelled ids of the roots of every triangle / aggregate kernel
+        and of the three CTA-tier modes (bit matrix, hash, binary search)."""
+        dp = self.dplus
+        cta = (dp > warp_maxd) & (dp <= TRI_CTA_MAXD)
+        big = dp > TRI_CTA_MAXD
+        return {"k_tri_warp": (dp >= 2) & (dp <= warp_maxd), "k_tri_cta": cta, "k_tri_big": big,
+                "big_bits": big & (dp <= TRI_BITS_MAXD), "big_hash": (dp > TRI_BITS_MAXD) & (dp <= TRI_HASH_MAXD),
+                "big_search": dp > TRI_HASH_MAXD}
+
+    def k4_bytes(self, max_pairs: float = 2.5e8):
+        """B_k4 = 4 * sum over oriented edges (u, v) and w in S = N+(u) ∩ N+(v)
+        of min(d+w, |S|), by listing the triangles u < v < w (every pair v < w
+        of N+(u) checked against the oriented edges); None when there are more
+        than max_pairs pairs to check. Returns (bytes or None, pairs, triangles)."""
+        n, ou, ov, dp = self.n, self.ou, self.ov, self.dplus
+        rowend = np.cumsum(np.bincount(ou, minlength=n))   # end index of each u's out-list in (ou, ov)
+        later = rowend[ou] - 1 - np.arange(len(ou))        # pairs (v, w), w after v in N+(u)
+        pairs = int(later.sum())
+        if pairs > max_pairs:
+            return None, pairs, None
+        keys = ou * n + ov                                 # sorted
+        total, ntri = 0, 0
+        idx = np.flatnonzero(later)
+        chunk = 1 << 22
+        s_count = np.zeros(len(ou), np.int64)              # |S(u, v)| per oriented edge index
+        hits_i, hits_w = [], []
+        # a hashed bitmap of the edge keys passes every edge and few others;
+        # only those are searched for exactly
+        hbits = int(min(28, max(16, np.ceil(np.log2(max(len(keys), 1) * 16)))))
+
+        def hsh(k):
+            return ((k.astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15)) >> np.uint64(64 - hbits)).astype(np.int64)
+
+        filt = np.zeros(1 << hbits, dtype=bool)
+        filt[hsh(keys)] = True
+        for c0 in range(0, len(idx), chunk):
+            ii = idx[c0:c0 + chunk]
+            cnt = later[ii]
+            rep = np.repeat(ii, cnt)
+            off = np.arange(len(rep)) - np.repeat(np.cumsum(cnt) - cnt, cnt) + 1
+            v, w = ov[rep], ov[rep + off]
+            q = v * n + w
+            cand = np.flatnonzero(filt[hsh(q)])
+            at = np.searchsorted(keys, q[cand])
+            at[at >= len(keys)] = 0
+            hit = cand[keys[at] == q[cand]]
+            hits_i.append(rep[hit])
+            hits_w.append(w[hit])
+        if hits_i:
+            hi = np.concatenate(hits_i)
+            hw = np.concatenate(hits_w)
+            np.add.at(s_count, hi, 1)
+            total = int(np.minimum(dp[hw], s_count[hi]).sum())
+            ntri = len(hi)
+        return 4 * total, pairs, ntri
+
+
+def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 1536, warp_maxd: int = 64,
+                      shape: "Shape | None" = None, with_k4: bool = True) -> dict:
     """Algorithmic byte counts (int32 = 4 B) in the relabel order, per stage
     and per kernel tier.
 
-    B_tri = 4 * sum over oriented edges (u, v) of min(d+u, d+v)
-    B_c4  = 4 * number of wedges u - v - w with v, w below u (cycle roots)
-    B_csr = 4 (n + 1) + 4 m, B_out = 120 n.
+    B_csr = 4 (n + 1) + 4 m, B_orient = 4 (n + 1) + 4 |E|,
+    B_tri = 4 * sum over oriented edges (u, v) of min(d+u, d+v),
+    B_k4  = 4 * sum over oriented edges (u, v), w in N+(u) ∩ N+(v) of
+            min(d+w, |N+(u) ∩ N+(v)|)  (None when too costly to list),
+    B_c4  = 4 * number of wedges u - v - w with v, w below u (cycle roots),
+    B_out = 120 n.
     A root's wedges (or triangle probes) count for the tier kernel that
-    takes it: 4-cycle roots by their wedge count W (with packed tables warp
-    <= 1152 and warp_big <= 1536, with split tables warp <= 576 and
-    warp_big <= 768; then packed mid <= 6144, split mid <= 3072, cta <=
-    12288, else global), triangle roots by out-degree (warp <= 64, cta <=
-    256, else big).
+    takes it (Shape.c4_tiers, Shape.tri_tiers).
     """
-    n = len(rowptr) - 1
-    m = len(colidx)
-    d = np.diff(rowptr).astype(np.int64)
-    order = np.lexsort((np.arange(n), deg_class(d)))
-    rank = np.empty(n, np.int64)
-    rank[order] = np.arange(n)
-    src = np.repeat(np.arange(n), d)
-    rs, rd = rank[src], rank[colidx.astype(np.int64)]
-    out = rd > rs
-    dplus = np.bincount(rs[out], minlength=n)
-    probes = np.minimum(dplus[rs[out]], dplus[rd[out]])
-    tri_root = rs[out]
+    sh = shape if shape is not None else Shape(rowptr, colidx)
+    n, m = sh.n, sh.m
+    probes = np.minimum(sh.dplus[sh.ou], sh.dplus[sh.ov])
+    droot = sh.dplus[sh.ou]
     b_tri = 4 * int(probes.sum())
-    droot = dplus[tri_root]
-    b_tri_cta = 4 * int(probes[(droot > warp_maxd) & (droot <= 256)].sum())
-    b_tri_big = 4 * int(probes[droot > 256].sum())
-    # wedges rooted at u through in-neighbour v: entries of row v below u
-    o2 = np.lexsort((rd, rs))
-    rs2, rd2 = rs[o2], rd[o2]
-    start = np.zeros(n + 1, np.int64)
-    start[1:] = np.cumsum(np.bincount(rs2, minlength=n))
-    pos = np.arange(m) - start[rs2]
-    sel = rd2 > rs2                                # entry (v -> u), u > v: pos wedges below u
-    w_root = np.bincount(rd2[sel], weights=pos[sel], minlength=n)
-    din = np.bincount(rd2[sel], minlength=n)
-    live = (din >= 2) & (w_root >= 2)
-    pack_lim = (1 << (32 - int(n - 1).bit_length())) - 2     # packed tables hold counts below this
-    # the warp tiers pack when the count bits reach their limit, else they
-    # use split tables of half as many slots; each takes W up to 3/4 of its
-    # slots (k_c4_warp 1536 words, k_c4_warp_big 2048)
-    packed = pack_lim >= c4_warp_ub
-    warp_lim = min(c4_warp_ub, 1152 if packed else 576)
-    big_lim = min(c4_warp_ub, 1536 if packed else 768)
-    warp = live & (w_root <= warp_lim)
-    wbig = live & ~warp & (w_root <= big_lim)
-    rest = live & ~warp & ~wbig
-    midp = rest & (w_root <= 6144) & (w_root <= pack_lim)
-    mid = rest & ~midp & (w_root <= 3072)
-    cta = rest & ~midp & ~mid & (w_root <= 12288)
-    tiers = {"k_c4_warp": warp, "k_c4_warp_big": wbig, "k_c4_midp": midp, "k_c4_mid": mid, "k_c4_cta": cta,
-             "k_c4_team": rest & (w_root > 12288)}
-    w_c4 = int(w_root.sum())
-    # B_k4 = 4 * sum over oriented edges (u, v) and w in S = N+(u) ∩ N+(v) of
-    # min(d+w, |S|): the probes for the edges inside each common out-
-    # neighbourhood. Computed for graphs up to 8e6 CSR entries with few
-    # oriented edges in a triangle (a sparse product, listed one by one);
-    # else None (for ER n = 1e6, mean degree 32, it is 19 748 bytes).
-    b_k4 = None
-    try:
-        if m > 8_000_000:
-            raise ImportError
-        import scipy.sparse as sp
-        ap = sp.csr_matrix((np.ones(len(rs[out]), np.int64), (rs[out], rd[out])), shape=(n, n))
-        ap.sort_indices()
-        s_uv = (ap @ ap.T).multiply(ap).tocoo()
-        if s_uv.nnz <= 200000:
-            tot = 0
-            ip, ix = ap.indptr, ap.indices
-            for a, b_, s in zip(s_uv.row, s_uv.col, s_uv.data):
-                common = np.intersect1d(ix[ip[a]:ip[a + 1]], ix[ip[b_]:ip[b_ + 1]], assume_unique=True)
-                tot += int(np.minimum(dplus[common], int(s)).sum())
-            b_k4 = 4 * tot
-    except ImportError:
-        pass
+    b_tri_cta = 4 * int(probes[(droot > warp_maxd) & (droot <= TRI_CTA_MAXD)].sum())
+    b_tri_big = 4 * int(probes[droot > TRI_CTA_MAXD].sum())
+    w_c4 = int(sh.w_root.sum())
+    b_k4, k4_pairs, ntri = sh.k4_bytes() if with_k4 else (None, None, None)
     res = {"B_csr": 4 * (n + 1) + 4 * m, "B_orient": 4 * (n + 1) + 2 * m, "B_tri": b_tri, "B_k4": b_k4,
-           "B_c4": 4 * w_c4, "W_c4": w_c4, "B_out": 120 * n, "tri_probes": b_tri // 4}
+           "B_c4": 4 * w_c4, "W_c4": w_c4, "B_out": 120 * n, "tri_probes": b_tri // 4,
+           "k4_pairs_checked": k4_pairs, "triangles": ntri}
     per_kernel = {"k_tri_warp": b_tri - b_tri_cta - b_tri_big, "k_tri_cta": b_tri_cta, "k_tri_big": b_tri_big,
                   "k_relabel_rows_warp": 2 * res["B_csr"], "k_solve": res["B_csr"] + res["B_out"]}
-    for k, msk in tiers.items():
-        per_kernel[k] = 4 * int(w_root[msk].sum())
+    for k, msk in sh.c4_tiers(c4_warp_ub).items():
+        per_kernel[k] = 4 * int(sh.w_root[msk].sum())
     res["per_kernel"] = per_kernel
+    return res
+
+
+def vertex_tiers(rowptr: np.ndarray, colidx: np.ndarray, shape: "Shape | None" = None) -> dict:
+    """Caller ids of the roots of every tier kernel (default launch shape)."""
+    sh = shape if shape is not None else Shape(rowptr, colidx)
+    res = {}
+    for k, msk in {**sh.tri_tiers(), **sh.c4_tiers()}.items():
+        res[k] = sh.order[np.flatnonzero(msk)]
     return res
 
 
@@ -223,15 +296,34 @@ def measured_peaks() -> dict:
     return {}
 
 
-def cpu_baseline(rowptr, colidx, edges) -> dict:
-    """The oracle on the host cores: the whole workload graph with all
-    threads, and one thread on a bounded sample of the same generator."""
+def cpu_baseline(rowptr, colidx, edges, got=None, batch=None) -> dict:
+    """The CPU leg: the oracle on the host cores.
+
+    Times the three-stage oracle on the whole workload graph with all host
+    threads (the reported baseline) and on a bounded sample with one thread.
+    Given `got` (the GPU counts of the same graph), compares every entry;
+    given `batch` = (graphs, GPU counts of their batched call, vertex
+    offsets), compares every graph of the batch with its oracle counts.
+    """
     import graphgen as gg
     import oracle
     cores = oracle.max_threads()
     t0 = time.perf_counter()
-    oracle.count(rowptr, colidx)
+    exp = oracle.count(rowptr, colidx)
     dt = time.perf_counter() - t0
+    parity = {}
+    if got is not None:
+        bad = int(np.count_nonzero(got != exp))
+        parity["workload"] = {"entries": int(exp.size), "mismatches": bad,
+                              "verdict": "bit-exact" if bad == 0 else "MISMATCH"}
+    if batch is not None:
+        graphs, bgot, vo = batch
+        t1 = time.perf_counter()
+        bad_graphs = [g for g, (rp, ci) in enumerate(graphs)
+                      if not np.array_equal(bgot[vo[g]:vo[g + 1]], oracle.count(rp, ci))]
+        parity["batched"] = {"graphs": len(graphs), "entries": int(bgot.size), "mismatched_graphs": len(bad_graphs),
+                             "verdict": "bit-exact" if not bad_graphs else "MISMATCH",
+                             "oracle_s": round(time.perf_counter() - t1, 1)}
     srp, sci = gg.er_mean_degree(REF_SAMPLE_N, MEAN_DEG, 1)
     oracle.set_threads(1)
     try:
@@ -245,7 +337,23 @@ def cpu_baseline(rowptr, colidx, edges) -> dict:
                       f"{dt:.1f} s",
             "single_thread": {"value": (len(sci) // 2) / dt1, "unit": UNIT, "cores": 1,
                               "sample": f"ER G(n={REF_SAMPLE_N}, mean degree {MEAN_DEG}), {len(sci) // 2} edges, "
-                                        f"{dt1:.1f} s"}}
+                                        f"{dt1:.1f} s"},
+            "parity": parity}
+
+
+def degree_invariants(rowptr, psi) -> list:
+    """Violated invariants of a count table that need only the degrees and
+    orbit sums (graphlet count x orbit size): empty when all hold."""
+    d = np.diff(np.asarray(rowptr)).astype(np.int64)
+    s = psi.sum(axis=0)
+    checks = {"psi0 = deg": np.array_equal(psi[:, 0], d), "psi2 = C(d,2)": np.array_equal(psi[:, 2], d * (d - 1) // 2),
+              "psi7 = C(d,3)": np.array_equal(psi[:, 7], d * (d - 1) * (d - 2) // 6),
+              "sum psi1 = 2 sum psi2": s[1] == 2 * s[2], "sum psi3 = 0 mod 3": s[3] % 3 == 0,
+              "sum psi4 = sum psi5": s[4] == s[5], "sum psi6 = 3 sum psi7": s[6] == 3 * s[7],
+              "sum psi8 = 0 mod 4": s[8] % 4 == 0, "sum psi10 = 2 sum psi9": s[10] == 2 * s[9],
+              "sum psi9 = sum psi11": s[9] == s[11], "sum psi12 = sum psi13": s[12] == s[13],
+              "sum psi14 = 0 mod 4": s[14] % 4 == 0, "nonnegative": bool((psi >= 0).all())}
+    return [k for k, ok in checks.items() if not ok]
 
 
 def dist_setup():
@@ -294,6 +402,232 @@ def run_reference(args) -> None:
     }), flush=True)
 
 
+class StepTimer:
+    """CUDA events around each step on the launching stream, with a 512 MB
+    write between steps so that no step starts with its inputs in L2."""
+
+    def __init__(self, dev, stream):
+        import torch
+        self.torch, self.dev, self.stream = torch, dev, stream
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def run(self, fn, steps: int, flush: bool = True) -> list:
+        torch = self.torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize(self.dev)
+        for i in range(steps):
+            if flush:
+                self.flush.fill_(i)
+            ev[i][0].record(self.stream)
+            fn()
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize(self.dev)
+        return [a.elapsed_time(b) for a, b in ev]
+
+
+def traced_kernel_ms(ni, fn, timer: StepTimer, steps: int) -> dict:
+    """{kernel: (ms per call, launches per call)} from the library's own
+    events on the call's stream, over `steps` calls separate from any timed
+    region (the timed regions run with tracing off)."""
+    ni.profile_reset()
+    ni.profile_enable(True)
+    try:
+        timer.run(fn, steps)
+    finally:
+        ni.profile_enable(False)
+    prof = ni.profile_read()
+    return {k: (v[0] / steps, v[1] / steps) for k, v in prof.items() if v[1] > 0}
+
+
+def roofline_terms(ab: dict, ms: float, peak: float) -> dict:
+    """Whole-call fractions of the HBM peak: compulsory (B_csr + B_out) and
+    algorithmic (B_csr + B_orient + B_tri + B_k4 + B_c4 + B_out)."""
+    bw = (ms * 1e-3) * 1e9 * peak
+    alg = ab["B_csr"] + ab["B_orient"] + ab["B_tri"] + (ab["B_k4"] or 0) + ab["B_c4"] + ab["B_out"]
+    res = {"compulsory_bytes": ab["B_csr"] + ab["B_out"], "compulsory_frac": (ab["B_csr"] + ab["B_out"]) / bw,
+           "algorithmic_bytes": alg, "algorithmic_frac": alg / bw,
+           "terms": {k: ab[k] for k in ("B_csr", "B_orient", "B_tri", "B_k4", "B_c4", "B_out")}}
+    if ab["B_k4"] is None:
+        res["B_k4_note"] = (f"omitted: listing the triangles it needs means checking {ab['k4_pairs_checked']:.3e} "
+                            f"out-neighbour pairs on the host; at most 4 B x that count")
+    return res
+
+
+def run_small_graph(ni, torch, dev, stream, timer, steps) -> dict:
+    """Latency of one call on ER G(2000, 0.01) (the small single-graph
+    configuration): eager, and replayed from a captured CUDA graph."""
+    import graphgen as gg
+    rp, ci = gg.er(2000, 0.01, 1)
+    d_rp, d_ci = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    out = torch.empty((len(rp) - 1, 15), dtype=torch.int64, device=dev)
+    for _ in range(5):
+        ni.count(d_rp, d_ci, out)
+    ni.check()
+    reps = max(steps, 50)
+    l0 = ni.launch_count()
+    eager = timer.run(lambda: ni.count(d_rp, d_ci, out), reps, flush=False)
+    launches = (ni.launch_count() - l0) / reps
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        ni.count(d_rp, d_ci, out, stream=side)
+    torch.cuda.synchronize(dev)
+    replay = timer.run(g.replay, reps, flush=False)
+    ni.check()
+    return {"workload": "Erdos-Renyi G(n=2000, p=0.01), seed 1", "edges": len(ci) // 2,
+            "us_per_call": statistics.median(eager) * 1e3, "us_per_call_cuda_graph": statistics.median(replay) * 1e3,
+            "launches_per_call": launches, "edges_per_s": (len(ci) // 2) / (statistics.median(eager) * 1e-3),
+            "invariants_violated": degree_invariants(rp, out.cpu().numpy()),
+            "_counts": out.cpu().numpy(), "_graph": (rp, ci)}
+
+
+def run_rmat(ni, torch, dev, stream, timer, steps, scale, peak) -> dict:
+    """The R-MAT configuration (power-law skew with hubs): edges/s, per-kernel
+    split and whole-call roofline fractions."""
+    import graphgen as gg
+    rp, ci = gg.rmat(scale, 16, seed=1)
+    edges = len(ci) // 2
+    d_rp, d_ci = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
+    out = torch.empty((len(rp) - 1, 15), dtype=torch.int64, device=dev)
+    for _ in range(3):
+        ni.count(d_rp, d_ci, out)
+    ni.check()
+    fn = lambda: ni.count(d_rp, d_ci, out)   # noqa: E731
+    step_ms = timer.run(fn, steps)
+    ni.check()
+    ms = sum(step_ms) / len(step_ms)
+    kern = traced_kernel_ms(ni, fn, timer, 2)
+    psi = out.cpu().numpy()
+    sh = Shape(rp, ci)
+    ab = algorithmic_bytes(rp, ci, shape=sh, with_k4=False)
+    _, pairs, _ = sh.k4_bytes(max_pairs=0)
+    ab["k4_pairs_checked"] = pairs
+    rl = roofline_terms(ab, ms, peak)
+    rl["per_kernel_frac"] = {k: round(ab["per_kernel"][k] / (kern[k][0] * 1e-3) / 1e9 / peak, 4)
+                             for k in ab["per_kernel"] if k in kern and ab["per_kernel"][k]}
+    return {"workload": f"R-MAT scale {scale}, edge factor 16, (.57,.19,.19,.05), seed 1; loops and duplicates removed",
+            "n": len(rp) - 1, "edges": edges, "steps": len(step_ms), "ms_per_call": ms, "edges_per_s": edges / (ms * 1e-3),
+            "triangles": int(psi[:, 3].sum() // 3), "kernel_ms": {k: round(v[0], 4) for k, v in
+                                                                  sorted(kern.items(), key=lambda kv: -kv[1][0])},
+            "roofline": rl, "invariants_violated": degree_invariants(rp, psi)}
+
+
+def run_batched(ni, torch, dev, stream, timer, steps, count) -> dict:
+    """The batched configuration: `count` Chung-Lu graphs in one call, the
+    same call replayed from a captured CUDA graph, and one call per graph."""
+    import graphgen as gg
+    graphs = gg.chunglu_batch(count, 2.5, 8.0, 50, 5000, seed=1)
+    rowptr, colidx, vo, eo = gg.pack(graphs)
+    d_rp = torch.from_numpy(rowptr.astype(np.int32)).to(dev)
+    d_ci = torch.from_numpy(colidx).to(dev)
+    d_vo, d_eo = torch.from_numpy(vo).to(dev), torch.from_numpy(eo).to(dev)
+    out = torch.empty((len(rowptr) - 1, 15), dtype=torch.int64, device=dev)
+    fn = lambda: ni.count_batch(d_rp, d_ci, d_vo, d_eo, out)   # noqa: E731
+    for _ in range(3):
+        fn()
+    ni.check()
+    ref = out.clone()
+    ms_eager = statistics.mean(timer.run(fn, steps))
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        ni.count_batch(d_rp, d_ci, d_vo, d_eo, out, stream=side)
+    torch.cuda.synchronize(dev)
+    out.zero_()
+    ms_graph = statistics.mean(timer.run(g.replay, steps))
+    replay_same = bool(torch.equal(out, ref))
+    singles = [(torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev),
+                torch.empty((len(r) - 1, 15), dtype=torch.int64, device=dev)) for r, c in graphs]
+
+    def one_per_launch():
+        for r, c, o in singles:
+            ni.count(r, c, o)
+
+    one_per_launch()
+    ms_single = statistics.mean(timer.run(one_per_launch, 2))
+    ni.check()
+    same_alone = all(torch.equal(o, ref[vo[i]:vo[i + 1]]) for i, (_, _, o) in enumerate(singles))
+    return {"workload": f"{count} Chung-Lu graphs, gamma 2.5, n log-uniform [50, 5000], mean degree 8, seed 1; "
+                        "packed CSR, one call",
+            "graphs": count, "vertices": int(vo[-1]), "edges": int(eo[-1] // 2),
+            "graphs_per_s_batched": count / (ms_eager * 1e-3), "graphs_per_s_cuda_graph": count / (ms_graph * 1e-3),
+            "graphs_per_s_one_per_launch": count / (ms_single * 1e-3), "ms_batched": ms_eager,
+            "ms_cuda_graph": ms_graph, "ms_one_per_launch": ms_single, "replay_bit_exact": replay_same,
+            "batched_equals_one_per_launch": bool(same_alone),
+            "_parity_input": (graphs, ref.cpu().numpy(), vo)}
+
+
+def serve_requests(nreq: int, max_edges: float):
+    """The served stream's requests: ER or Chung-Lu (gamma in [2.2, 3.0]),
+    |E| log-uniform in [1e3, max_edges], mean degree uniform in [4, 32]."""
+    import graphgen as gg
+    u = gg.uniform(1, 11, 4 * nreq)
+    graphs = []
+    for i in range(nreq):
+        e = float(np.exp(np.log(1e3) + u[i] * (np.log(max_edges) - np.log(1e3))))
+        dmean = 4 + 28 * u[nreq + i]
+        n = max(int(2 * e / dmean), 8)
+        if u[2 * nreq + i] < 0.5:
+            graphs.append(gg.er_mean_degree(n, dmean, 100 + i))
+        else:
+            graphs.append(gg.chunglu(n, 2.2 + 0.8 * u[3 * nreq + i], dmean, 100 + i))
+    return graphs
+
+
+def run_served(ni, torch, dev, nreq, max_edges, budget_gb) -> dict:
+    """The served stream: Poisson arrivals at 50/80/95% of the measured
+    capacity through the continuous-batching server, p50/p99 latency (submit
+    to counts in host memory) and graphs/s, against one call per request."""
+    import zlib
+
+    import graphgen as gg
+    from paper_2606_29651_gb300.serve import Server, latency_stats
+    graphs = serve_requests(nreq, max_edges)
+    total_edges = sum(len(c) // 2 for _, c in graphs)
+    by_load = {}
+    crc_served = None
+    with Server(dev.index or 0, mem_budget=budget_gb << 30) as srv:   # staging buffers persist
+        for f in [srv.submit(rp, ci) for rp, ci in graphs]:          # warm-up: buffers reach size
+            f.result()
+        t0 = time.perf_counter()                                      # capacity: all submitted at once
+        futs = [srv.submit(rp, ci) for rp, ci in graphs]
+        for f in futs:
+            f.result()
+        cap = nreq / (time.perf_counter() - t0)
+        for rho in (0.5, 0.8, 0.95):
+            lam = rho * cap
+            gaps = -np.log(1.0 - gg.uniform(2, int(rho * 100), nreq)) / lam
+            b0 = srv.batches
+            futs = []
+            t0 = time.perf_counter()
+            t_next = t0
+            for i, (rp, ci) in enumerate(graphs):
+                t_next += gaps[i]
+                while time.perf_counter() < t_next:
+                    time.sleep(0)
+                futs.append(srv.submit(rp, ci))
+            res = [f.result() for f in futs]
+            span = time.perf_counter() - t0
+            lat = [f.request.t_done - f.request.t_submit for f in futs]
+            by_load[str(rho)] = dict(arrival_graphs_per_s=lam, graphs_per_s=nreq / span,
+                                     edges_per_s=total_edges / span, batches=srv.batches - b0, **latency_stats(lat))
+            crc_served = [zlib.crc32(np.ascontiguousarray(r).tobytes()) for r in res]
+    t0 = time.perf_counter()
+    crc_alone = []
+    for rp, ci in graphs:
+        o = ni.count(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)).cpu().numpy()
+        crc_alone.append(zlib.crc32(o.tobytes()))
+    one_by_one = nreq / (time.perf_counter() - t0)
+    ni.check()
+    return {"workload": f"{nreq} Poisson requests, ER / Chung-Lu (gamma 2.2-3.0), |E| log-uniform [1e3, "
+                        f"{max_edges:.0e}], mean degree 4-32, seed 1; admission by a {budget_gb} GB device budget",
+            "requests": nreq, "total_edges": total_edges, "capacity_graphs_per_s": cap,
+            "one_call_per_request_graphs_per_s": one_by_one, "by_load": by_load,
+            "served_equals_alone": crc_served == crc_alone}
+
+
 def run_ours(args) -> None:
     import torch
 
@@ -315,8 +649,9 @@ def run_ours(args) -> None:
     d_rp = torch.from_numpy(rp).to(dev)
     d_ci = torch.from_numpy(ci).to(dev)
     out = torch.empty((n, 15), dtype=torch.int64, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)   # 512 MB > L2
     stream = torch.cuda.current_stream(dev)
+    timer = StepTimer(dev, stream)
+    fn = lambda: ni.count(d_rp, d_ci, out)   # noqa: E731
 
     uuid = None
     try:
@@ -326,40 +661,30 @@ def run_ours(args) -> None:
         uuid = None
 
     for _ in range(args.warmup):
-        ni.count(d_rp, d_ci, out)
+        fn()
     torch.cuda.synchronize(dev)
     ni.check()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ni.profile_reset()
-    ni.profile_enable(True)
+    # the timed region: tracing off, L2 flushed between steps
+    ni.profile_enable(False)
     with ClockSampler(uuid) as clocks:
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
         launches0 = ni.launch_count()
-        for i in range(args.steps):
-            flush.fill_(i)                       # evict the graph from L2 between steps
-            starts[i].record(stream)
-            ni.count(d_rp, d_ci, out)
-            ends[i].record(stream)
-        torch.cuda.synchronize(dev)
+        step_ms = timer.run(fn, args.steps)
         launches = ni.launch_count() - launches0
         if world > 1:
             torch.distributed.barrier()
         time.sleep(0.3)
-    ni.profile_enable(False)
     ni.check()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(step_ms) / len(step_ms)
     ms = reduce_max(ms, world, dev)
     value = world * edges / (ms * 1e-3)
-
-    # per-kernel times over the timed region
-    prof = {k: v for k, v in ni.profile_read().items() if v[1] > 0}
-    top_name, (top_ms, top_calls) = max(prof.items(), key=lambda kv: kv[1][0])
-    top_avg_ms = top_ms / top_calls
+    # per-kernel split from a separate traced pass of the same steps
+    kern = traced_kernel_ms(ni, fn, timer, args.steps)
+    traced_ms = sum(v[0] for v in kern.values())
+    top_name, (top_avg_ms, _) = max(kern.items(), key=lambda kv: kv[1][0])
 
     # End to end through the public call with the graph and the counts in
     # pinned host memory: niorca_count_host reads the CSR and writes the
@@ -369,32 +694,23 @@ def run_ours(args) -> None:
     h_rp = torch.from_numpy(rp).pin_memory()
     h_ci = torch.from_numpy(ci).pin_memory()
     h_out = torch.empty((n, 15), dtype=torch.int64).pin_memory()
-    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(i)
-        e_s[i].record(stream)
-        ni.count_host(h_rp, h_ci, h_out)
-        e_e[i].record(stream)
-    torch.cuda.synchronize(dev)
+    e2e_ms = statistics.mean(timer.run(lambda: ni.count_host(h_rp, h_ci, h_out), args.steps))
     ni.check()
-    e2e_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
-    if not torch.equal(h_out, out.cpu()):
+    got = out.cpu().numpy()
+    if not np.array_equal(h_out.numpy(), got):
         raise RuntimeError("end-to-end output differs from the resident-input output")
     h_out2 = torch.empty((n, 15), dtype=torch.int64).pin_memory()
     e_rp = torch.empty_like(d_rp)
     e_ci = torch.empty_like(d_ci)
-    for i in range(args.steps):
-        flush.fill_(i)
-        e_s[i].record(stream)
+
+    def staged():
         e_rp.copy_(h_rp, non_blocking=True)
         e_ci.copy_(h_ci, non_blocking=True)
         ni.count(e_rp, e_ci, out)
         h_out2.copy_(out, non_blocking=True)
-        e_e[i].record(stream)
-    torch.cuda.synchronize(dev)
+
+    staged_ms = statistics.mean(timer.run(staged, args.steps))
     ni.check()
-    staged_ms = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / args.steps
     e2e_ms = reduce_max(e2e_ms, world, dev)
     staged_ms = reduce_max(staged_ms, world, dev)
     if not torch.equal(h_out2, h_out):
@@ -405,31 +721,23 @@ def run_ours(args) -> None:
             torch.distributed.destroy_process_group()
         return
 
-    tun = ni.get_tuning()
-    ab = algorithmic_bytes(rp, ci, tun["c4_warp_maxw"], tun["warp_maxd"])
     peaks = measured_peaks()
-    peak = peaks.get("hbm_gbs")
+    peak = peaks.get("hbm_gbs") or 6800.0
+    tun = ni.get_tuning()
+    sh = Shape(rp, ci)
+    ab = algorithmic_bytes(rp, ci, tun["c4_warp_maxw"], tun["warp_maxd"], shape=sh)
     alg = ab["per_kernel"].get(top_name)
     achieved = alg / (top_avg_ms * 1e-3) / 1e9 if alg else None
     roofline = {
-        "bound": "hbm", "kernel": top_name, "achieved": achieved,
-        "peak": peak if peak else 6800.0, "unit": "GB/s",
-        "frac": (achieved / (peak if peak else 6800.0)) if achieved else None,
-        "traffic": ncu_traffic(top_name),
-        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak else "fallback 6.8 TB/s",
+        "bound": "hbm", "kernel": top_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic(top_name),
+        "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s",
         "algorithmic_bytes_per_launch": alg, "avg_launch_ms": top_avg_ms,
-        "kernel_ms_per_step": {k: round(v[0] / v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "kernel_timing": f"library events on the call's stream, {args.steps} traced calls after the timed region "
+                         f"(their kernels sum to {traced_ms:.3f} ms per call)",
+        "kernel_ms_per_step": {k: round(v[0], 4) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])},
+        "whole_call": roofline_terms(ab, ms, peak),
     }
-    # whole-call fractions of the same peak: compulsory = (B_csr + B_out);
-    # algorithmic = (B_csr + B_orient + B_tri + B_k4 + B_c4 + B_out)
-    bw = (ms * 1e-3) * 1e9 * (peak if peak else 6800.0)
-    alg_total = ab["B_csr"] + ab["B_orient"] + ab["B_tri"] + (ab["B_k4"] or 0) + ab["B_c4"] + ab["B_out"]
-    roofline["whole_call"] = {
-        "compulsory_bytes": ab["B_csr"] + ab["B_out"], "compulsory_frac": (ab["B_csr"] + ab["B_out"]) / bw,
-        "algorithmic_bytes": alg_total, "algorithmic_frac": alg_total / bw,
-        "terms": {k: ab[k] for k in ("B_csr", "B_orient", "B_tri", "B_k4", "B_c4", "B_out")},
-    }
-    cpu = None if args.no_cpu_baseline else cpu_baseline(rp, ci, edges)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -446,174 +754,35 @@ def run_ours(args) -> None:
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
         "roofline": roofline,
-        "cpu_baseline": cpu,
     }
+    extras_ok = True
+    batch_parity = None
+    if world == 1 and not args.no_extras:
+        def guarded(name, f):
+            try:
+                return f()
+            except Exception as e:   # an extra that fails is recorded, the headline stands
+                return {"error": f"{type(e).__name__}: {e}"}
+        small = guarded("small_graph", lambda: run_small_graph(ni, torch, dev, stream, timer, args.steps))
+        line["small_graph"] = {k: v for k, v in small.items() if not k.startswith("_")}
+        line[f"rmat{args.rmat_scale}"] = guarded("rmat", lambda: run_rmat(ni, torch, dev, stream, timer,
+                                                                          min(args.steps, 5), args.rmat_scale, peak))
+        bat = guarded("batched", lambda: run_batched(ni, torch, dev, stream, timer, min(args.steps, 10),
+                                                     args.batch_graphs))
+        batch_parity = bat.pop("_parity_input", None)
+        line["batched"] = bat
+        line["served"] = guarded("served", lambda: run_served(ni, torch, dev, args.serve_requests,
+                                                             args.serve_max_edges, args.serve_budget_gb))
+    cpu = None if args.no_cpu_baseline else cpu_baseline(rp, ci, edges, got=got, batch=batch_parity)
+    line["cpu_baseline"] = cpu
+    if cpu is not None:
+        line["parity"] = {k: v["verdict"] for k, v in cpu["parity"].items()}
+        extras_ok = all(v["verdict"] == "bit-exact" for v in cpu["parity"].values())
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
-def run_single_config(args) -> None:
-    """Other single-graph configurations (not the headline): ER2000, RMAT22."""
-    import torch
-
-    import graphgen as gg
-    import paper_2606_29651_gb300 as ni
-    dev = torch.device("cuda", 0)
-    ni.build()
-    if args.workload == "er2000":
-        rp, ci = gg.er(2000, 0.01, 1)
-        desc = "Erdos-Renyi G(n=2000, p=0.01), seed 1"
-    else:
-        rp, ci = gg.rmat(args.rmat_scale, 16, seed=1)
-        desc = f"R-MAT scale {args.rmat_scale}, edge factor 16, (.57,.19,.19,.05), seed 1"
-    edges = len(ci) // 2
-    d_rp, d_ci = torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev)
-    out = torch.empty((len(rp) - 1, 15), dtype=torch.int64, device=dev)
-    for _ in range(args.warmup):
-        ni.count(d_rp, d_ci, out)
-    torch.cuda.synchronize()
-    ni.check()
-    ni.profile_reset()
-    ni.profile_enable(True)
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(args.steps):
-        ni.count(d_rp, d_ci, out)
-    e.record()
-    torch.cuda.synchronize()
-    ni.profile_enable(False)
-    ms = s.elapsed_time(e) / args.steps
-    prof = {k: round(v[0] / v[1], 4) for k, v in ni.profile_read().items() if v[1]}
-    # latency of one call without timing events (launch-bound at this size)
-    ni.check()
-    print(json.dumps({"workload": desc, "edges": edges, "ms_per_call": ms, "edges_per_s": edges / (ms * 1e-3),
-                      "kernel_ms": prof}), flush=True)
-
-
-def run_batch(args) -> None:
-    """Config 4: 8192 Chung-Lu graphs, one batched call; captured CUDA graph
-    replay; against one niorca_count launch sequence per graph."""
-    import torch
-
-    import graphgen as gg
-    import paper_2606_29651_gb300 as ni
-    dev = torch.device("cuda", 0)
-    ni.build()
-    count = args.batch_graphs
-    graphs = gg.chunglu_batch(count, 2.5, 8.0, 50, 5000, seed=1)
-    rowptr, colidx, vo, eo = gg.pack(graphs)
-    d_rp = torch.from_numpy(rowptr.astype(np.int32)).to(dev)
-    d_ci = torch.from_numpy(colidx).to(dev)
-    d_vo, d_eo = torch.from_numpy(vo).to(dev), torch.from_numpy(eo).to(dev)
-    out = torch.empty((len(rowptr) - 1, 15), dtype=torch.int64, device=dev)
-    for _ in range(args.warmup):
-        ni.count_batch(d_rp, d_ci, d_vo, d_eo, out)
-    torch.cuda.synchronize()
-    ni.check()
-    ref = out.clone()
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record()
-    for _ in range(args.steps):
-        ni.count_batch(d_rp, d_ci, d_vo, d_eo, out)
-    e.record()
-    torch.cuda.synchronize()
-    ms_eager = s.elapsed_time(e) / args.steps
-    # captured once, replayed
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        ni.count_batch(d_rp, d_ci, d_vo, d_eo, out)
-    g.replay()
-    torch.cuda.synchronize()
-    s.record()
-    for _ in range(args.steps):
-        g.replay()
-    e.record()
-    torch.cuda.synchronize()
-    ms_graph = s.elapsed_time(e) / args.steps
-    same = bool(torch.equal(out, ref))
-    # one graph per launch sequence, same GPU, graphs already resident
-    singles = [(torch.from_numpy(r).to(dev), torch.from_numpy(c).to(dev),
-                torch.empty((len(r) - 1, 15), dtype=torch.int64, device=dev)) for r, c in graphs]
-    for r, c, o in singles[:64]:
-        ni.count(r, c, o)
-    torch.cuda.synchronize()
-    s.record()
-    for r, c, o in singles:
-        ni.count(r, c, o)
-    e.record()
-    torch.cuda.synchronize()
-    ms_single = s.elapsed_time(e)
-    ni.check()
-    print(json.dumps({
-        "workload": f"batched: {count} Chung-Lu graphs, gamma 2.5, n log-uniform [50, 5000], mean degree 8",
-        "graphs": count, "vertices": int(vo[-1]), "edges": int(eo[-1] // 2),
-        "graphs_per_s_batched": count / (ms_eager * 1e-3), "graphs_per_s_cuda_graph": count / (ms_graph * 1e-3),
-        "graphs_per_s_one_per_launch": count / (ms_single * 1e-3), "ms_batched": ms_eager,
-        "ms_cuda_graph": ms_graph, "ms_one_per_launch": ms_single, "replay_bit_exact": same}), flush=True)
-
-
-def run_serve(args) -> None:
-    """Config 5: Poisson arrivals of ER / Chung-Lu graphs, continuous batching."""
-    import graphgen as gg
-    import paper_2606_29651_gb300 as ni
-    from paper_2606_29651_gb300.serve import Server, latency_stats
-    ni.build()
-    nreq = args.serve_requests
-    u = gg.uniform(1, 11, 4 * nreq)
-    graphs = []
-    for i in range(nreq):
-        e = float(np.exp(np.log(1e3) + u[i] * (np.log(args.serve_max_edges) - np.log(1e3))))
-        dmean = 4 + 28 * u[nreq + i]
-        n = max(int(2 * e / dmean), 8)
-        if u[2 * nreq + i] < 0.5:
-            graphs.append(gg.er_mean_degree(n, dmean, 100 + i))
-        else:
-            graphs.append(gg.chunglu(n, 2.2 + 0.8 * u[3 * nreq + i], dmean, 100 + i))
-    total_edges = sum(len(c) // 2 for _, c in graphs)
-    budget = args.serve_budget_gb << 30
-    by_load = {}
-    with Server(0, mem_budget=budget) as srv:          # one server throughout: staging buffers stay
-        for f in [srv.submit(rp, ci) for rp, ci in graphs]:   # warm-up pass: buffers reach size
-            f.result()
-        t0 = time.perf_counter()                        # capacity: everything submitted at once
-        futs = [srv.submit(rp, ci) for rp, ci in graphs]
-        for f in futs:
-            f.result()
-        cap = nreq / (time.perf_counter() - t0)
-        for rho in (0.5, 0.8, 0.95):
-            lam = rho * cap
-            gaps = -np.log(1.0 - gg.uniform(2, int(rho * 100), nreq)) / lam
-            b0 = srv.batches
-            futs = []
-            t0 = time.perf_counter()
-            t_next = t0
-            for i, (rp, ci) in enumerate(graphs):
-                t_next += gaps[i]
-                while time.perf_counter() < t_next:
-                    time.sleep(0)
-                futs.append(srv.submit(rp, ci))
-            for f in futs:
-                f.result()
-            span = time.perf_counter() - t0
-            lat = [f.request.t_done - f.request.t_submit for f in futs]
-            by_load[str(rho)] = dict(graphs_per_s=nreq / span, edges_per_s=total_edges / span,
-                                     batches=srv.batches - b0, **latency_stats(lat))
-    # the same requests one call at a time, no batching
-    import torch
-    dev = torch.device("cuda", 0)
-    t0 = time.perf_counter()
-    for rp, ci in graphs:
-        o = ni.count(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
-        o.cpu()
-    one_by_one = nreq / (time.perf_counter() - t0)
-    print(json.dumps({"workload": f"served: {nreq} Poisson requests, ER / Chung-Lu (gamma 2.2-3.0), "
-                                  f"|E| log-uniform [1e3, {args.serve_max_edges:.0e}]",
-                      "total_edges": total_edges, "capacity_graphs_per_s": cap,
-                      "one_call_per_request_graphs_per_s": one_by_one, "by_load": by_load}), flush=True)
+    if not extras_ok:
+        raise SystemExit("parity: GPU counts differ from the oracle")
 
 
 def main() -> None:
@@ -623,8 +792,8 @@ def main() -> None:
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["er1e6", "er2000", "rmat22", "batch", "serve"], default="er1e6",
-                    help="er1e6 is the headline line; the others print their own records")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: skip the small-graph, R-MAT, batched and served records")
     ap.add_argument("--batch-graphs", type=int, default=8192)
     ap.add_argument("--rmat-scale", type=int, default=22)
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -635,14 +804,8 @@ def main() -> None:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "er1e6":
-        run_ours(args)
-    elif args.workload in ("er2000", "rmat22"):
-        run_single_config(args)
-    elif args.workload == "batch":
-        run_batch(args)
     else:
-        run_serve(args)
+        run_ours(args)
 
 
 if __name__ == "__main__":

@@ -28,9 +28,10 @@
  *     once the stream has reached the end of the call's work.
  *   - Argument errors are returned synchronously and nothing is enqueued.
  *     Errors found on the device (malformed CSR, too large a degree) are
- *     recorded in a per-device status word, read by niorca_last_status();
- *     after such an error `out` is unspecified. Malformed input never makes
- *     a kernel access memory outside the given arrays.
+ *     recorded in the status word of the call's stream, read by
+ *     niorca_last_status(stream); after such an error `out` is unspecified.
+ *     Malformed input never makes a kernel access memory outside the given
+ *     arrays: a degree above 2^20 stops every stage after the degree pass.
  *   - Work memory is taken from a library-owned, stream-ordered pool on the
  *     current device and returned to it when the stream reaches the end of
  *     the call; the pool keeps freed memory for reuse.
@@ -134,10 +135,16 @@ niorca_status niorca_count_batch(const int32_t *rowptr, const int32_t *colidx, c
 niorca_status niorca_validate(const int32_t *rowptr, const int32_t *colidx, int32_t n, int64_t m, void *stream);
 
 /*
- * Synchronises `stream`, then returns and clears the device status word of
- * the current device: the first error that any call recorded on the device
- * since the previous read (NIORCA_OK if none), or NIORCA_ECUDA if the
- * stream itself reports an error.
+ * Reads and clears the status word of `stream` on the current device, in
+ * the stream's order, and synchronises the stream: the errors that calls
+ * enqueued on this stream recorded since the previous read (NIORCA_OK if
+ * none; the lowest code if several), or NIORCA_ECUDA if the stream itself
+ * reports an error. Calls on other streams never set or clear this word, so
+ * concurrent calls on separate streams report separately. A call captured
+ * into a CUDA graph reports into the word of the stream it was captured on.
+ * The library holds 4096 words per device; beyond 4096 distinct streams,
+ * streams share words (by a hash of the handle) and may see each other's
+ * errors.
  */
 niorca_status niorca_last_status(void *stream);
 
@@ -208,6 +215,13 @@ int32_t niorca_version(void);
  *         (1..127; default 32, i.e. degree >= 512)
  *   6     largest wedge count W of a 4-cycle root handled by one warp (2..1536)
  *   7     largest out-degree of a triangle root handled by one warp (2..64)
+ *   8     largest out-degree of a CTA-tier triangle root that keeps the bit
+ *         matrix of its out-neighbourhood (2..1152; default 1152)
+ *   9     largest out-degree of a CTA-tier triangle root that hashes its
+ *         out-neighbourhood in shared memory; above it, binary searches
+ *         (2..8192; default 8192)
+ *   10    4-cycle roots with more wedges than this are counted by the
+ *         key-tiled tier (2..12288; default 12288)
  * Any setting gives the same counts; only the speed changes. Returns
  * NIORCA_EINVAL (and changes nothing) for a value out of range.
  * niorca_get_tuning copies the current values and returns how many exist.

@@ -205,12 +205,14 @@ def validate(rowptr: torch.Tensor, colidx: torch.Tensor, stream=None) -> None:
 
 
 def last_status(stream=None) -> Status:
-    """Synchronise the stream and return (and clear) the device status."""
+    """Read and clear the status word of `stream` (default: torch's current
+    stream) after the stream's work; errors of calls on other streams are
+    not seen here."""
     return Status(_lib().niorca_last_status(_stream_ptr(stream)))
 
 
 def check(stream=None) -> None:
-    """Raise NiorcaError if a device-side error was recorded."""
+    """Raise NiorcaError if a call on `stream` recorded a device-side error."""
     st = _lib().niorca_last_status(_stream_ptr(stream))
     if st:
         raise NiorcaError(st, "device status")
@@ -253,7 +255,7 @@ def launch_count() -> int:
 
 
 TUNING_KEYS = ("grid_relabel", "grid_tri", "grid_agg", "grid_c4", "grid_solve", "long_row_class", "c4_warp_maxw",
-               "warp_maxd")
+               "warp_maxd", "tri_bits_maxd", "tri_hash_maxd", "c4_team_minw")
 
 
 def get_tuning() -> dict:

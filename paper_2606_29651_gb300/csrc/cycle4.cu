@@ -14,16 +14,15 @@
 // ending at the position of u, which a search of N+(v) finds. Roots are
 // routed by their wedge count W (a count is at most W too): one warp with a
 // 6 KB table (k_c4_warp) or an 8 KB one (k_c4_warp_big), four warps
-// (k_c4_midp / k_c4_mid), a 512-thread CTA (k_c4_cta), or a cluster of
-// CTAs sharing a dense count row in global memory (k_c4_team). The other tables are open-addressing hash tables in
-// shared memory, either split (key and count arrays) or packed (key << cb |
-// count in one 32-bit word, cb = 32 - bits(n - 1) count bits, usable while
-// W < 2^cb - 1), which holds twice the keys in the same space. Each table
-// is emptied once per CTA; afterwards a warp sweeps the region its root
-// used, and a CTA empties the slots it filled (kept in a 16-bit `touched`
-// list).
-#include <cooperative_groups.h>
-
+// (k_c4_midp / k_c4_mid), a 512-thread CTA (k_c4_cta), or, for the largest
+// roots, a 1024-thread CTA that counts the root's key range tile by tile in
+// shared memory (k_c4_tiled). The other tables are open-addressing hash
+// tables in shared memory, either split (key and count arrays) or packed
+// (key << cb | count in one 32-bit word, cb = 32 - bits(n - 1) count bits,
+// usable while W < 2^cb - 1), which holds twice the keys in the same space.
+// Each table is emptied once per CTA; afterwards a warp sweeps the region
+// its root used, and a CTA empties the slots it filled (kept in a 16-bit
+// `touched` list).
 #include "kernels.h"
 
 namespace niorca {
@@ -41,10 +40,6 @@ constexpr int CM_MAXW = 3072;      // split; 6144 when packed
 constexpr int CC_THREADS = 512;
 constexpr int CC_SLOTS = 16384;     // split
 constexpr int CC_MAXW = 12288;
-constexpr int CT_THREADS = 1024;   // team tier: CTAs of a cluster share one dense row
-constexpr int CT_CLUSTER = 8;
-constexpr int CT_MAXCH = (1 << 20) / 32;   // chunks of 32 in-neighbours (degree <= 2^20)
-constexpr size_t CT_SMEM = (size_t)(CT_MAXCH + 1) * 4;
 constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
@@ -381,7 +376,9 @@ __host__ __device__ constexpr int cw_maxw(bool split, int words) { return cw_slo
 // rest for the wider tiers. SPLIT: (key, count) pair tables, for graphs
 // whose ids leave a packed word too few count bits.
 template <bool SPLIT, bool BIG>
-__device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, int *counters, int maxw, int cb) {
+__device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, int *counters, int maxw, int cb,
+                                             int teamw) {
+    if (degree_overflow(counters)) return;
     constexpr int WORDS = BIG ? CWB_WORDS : CW_WORDS;
     constexpr int TS = cw_slots(SPLIT, WORDS);
     __shared__ C4WarpSmem<WORDS> sm_all[CW_WARPS];
@@ -455,11 +452,13 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
                 if (lane == 0) {
                     int which, list;   // queue counter and list slot (lists + list * n)
                     if (!BIG && W <= big_lim) { which = CNT_C4_WBIG; list = CW_BIG_LIST; }
-                    else if (W > CC_MAXW) { which = CNT_C4_TEAM; list = 4; }
+                    else if (W > teamw) { which = CNT_C4_TEAM; list = 4; }
                     else if (W <= 2 * CM_MAXW && W <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
                     else if (W <= CM_MAXW) { which = CNT_C4_MID; list = 2; }
                     else { which = CNT_C4_CTA; list = 3; }
-                    lists[(size_t)list * g.n + atomicAdd(&counters[which], 1)] = u;
+                    const int at = atomicAdd(&counters[which], 1);
+                    lists[(size_t)list * g.n + at] = u;
+                    if (which == CNT_C4_TEAM) lists[(size_t)g.n + at] = (int)W;   // the order of the key-tiled tier
                 }
                 return;
             }
@@ -486,23 +485,23 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
 
 // 8 CTAs of 4 warps per SM: 6 KB tables and at most 64 registers a thread.
 __global__ void __launch_bounds__(CW_WARPS * 32, 8) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters,
-                                                              int maxw, int cb) {
-    c4_warp_body<false, false>(g, vacc, lists, counters, maxw, cb);
+                                                              int maxw, int cb, int teamw) {
+    c4_warp_body<false, false>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
 __global__ void __launch_bounds__(CW_WARPS * 32, 8) k_c4_warp_split(Graph g, VAcc *vacc, int *lists,
-                                                                    int *counters, int maxw, int cb) {
-    c4_warp_body<true, false>(g, vacc, lists, counters, maxw, cb);
+                                                                    int *counters, int maxw, int cb, int teamw) {
+    c4_warp_body<true, false>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_big(Graph g, VAcc *vacc, int *lists, int *counters,
-                                                               int maxw, int cb) {
-    c4_warp_body<false, true>(g, vacc, lists, counters, maxw, cb);
+                                                               int maxw, int cb, int teamw) {
+    c4_warp_body<false, true>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_big_split(Graph g, VAcc *vacc, int *lists,
-                                                                     int *counters, int maxw, int cb) {
-    c4_warp_body<true, true>(g, vacc, lists, counters, maxw, cb);
+                                                                     int *counters, int maxw, int cb, int teamw) {
+    c4_warp_body<true, true>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
 // Roots from a queue, one CTA each. The table (SLOTS split slots, or
@@ -550,179 +549,287 @@ constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXW);
 
 __global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists,
                                                        const int *counters, int cb) {
+    if (degree_overflow(counters)) return;
     c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
 }
 
 __global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, VAcc *vacc, const int *lists,
                                                         const int *counters, int cb) {
+    if (degree_overflow(counters)) return;
     c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
 }
 
 __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists,
                                                        const int *counters, int cb) {
+    if (degree_overflow(counters)) return;
     c4_queue<CC_THREADS, CC_SLOTS, CC_MAXW, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
 }
 
-// Zero the dense rows of the team tier (only when that tier has work).
-__global__ void k_c4_zero_dense(int *dense, long long words, const int *counters) {
-    if (counters[CNT_C4_TEAM] == 0) return;
-    int4 *d4 = reinterpret_cast<int4 *>(dense);
-    const long long n4 = words / 4;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
-        d4[i] = make_int4(0, 0, 0, 0);
-    for (long long i = n4 * 4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < words;
-         i += (long long)gridDim.x * blockDim.x)
-        dense[i] = 0;
-}
+// ------------------------------------------------------ key-tiled tier
+//
+// Roots with more wedges than the hash tiers take (W > teamw): one CTA per
+// root, largest roots first. The keys w of a root u are the vertices below
+// u; the CTA cuts them into tiles of TK consecutive ids and counts each
+// tile's wedges in shared memory (16-bit counters while the root has fewer
+// than 65535 in-neighbours, as no count exceeds that; 32-bit ones, half as
+// many keys, above). A root's wedges through its in-neighbour v are the
+// entries of row v below u, ascending, so the wedges that fall into a tile
+// are a run of that row: every in-neighbour keeps a cursor (the start of its
+// next run) and the end of its wedge prefix, and a tile's run is found by a
+// galloping search from the cursor. Each tile takes three steps: count its
+// wedges, credit C(c, 2) to every key w and to u from the counts, walk the
+// runs again adding c - 1 per wedge to its middle vertex, then clear. The
+// next tile starts at the smallest key any cursor points at, so key ranges
+// without wedges are skipped.
+// The cursors of all these roots (their in-degrees sum to at most |E|) live
+// in the per-edge triangle counts, which nothing reads after the aggregate
+// stage: two ints per in-neighbour, |E| pairs in m ints.
+constexpr int CK_THREADS = 1024;
+constexpr int CK_NW = CK_THREADS / 32;
+constexpr int CK_WORDS = 48 * 1024;                 // counter words in shared memory (192 KB)
+constexpr int CK_NARROW_MAXD = 65534;               // in-degree up to which 16-bit counters cannot overflow
+constexpr int CK_INF = 0x7fffffff;
+constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + 64;
+static_assert(CK_SMEM <= 227 * 1024, "k_c4_tiled shared memory");
 
-// Roots with W > CC_MAXW: one cluster of CT_CLUSTER CTAs per root, counting
-// in a dense row of n ints in global memory that the cluster shares, so
-// that only one row per cluster is live. The root's wedges, in the order
-// of its in-neighbours, are cut into equal slices, one per warp of the
-// cluster; every CTA keeps the prefix sums of the wedge counts of the
-// root's 32-in-neighbour chunks (W < 2^31: a root's wedges are entries of
-// rows of the CSR) to find where a slice starts.
-// Pass 1 adds every wedge; pass 2 reads each count (per middle vertex) and
-// marks the key with the sign bit, so that exactly one visitor credits
-// C(c, 2) to w; pass 3 stores zeros back. Cluster barriers separate the
-// passes.
-__global__ void __cluster_dims__(CT_CLUSTER, 1, 1) __launch_bounds__(CT_THREADS)
-    k_c4_team(Graph g, VAcc *vacc, const int *lists, const int *counters, int *dense, int teams) {
-    namespace cg = cooperative_groups;
-    cg::cluster_group cluster = cg::this_cluster();
-    constexpr int NW = CT_THREADS / 32;
-    constexpr int SLICES = NW * CT_CLUSTER;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    int *P = reinterpret_cast<int *>(dsm);   // chunk prefix sums, CT_MAXCH + 1
-    __shared__ SegTab segs[NW];
-    __shared__ long long pvs[NW][32];
-    __shared__ int wsum[NW];
-    const int team = blockIdx.x / CT_CLUSTER;
-    const int wid = threadIdx.x >> 5, lane = lane_id();
-    const int slice = (int)cluster.block_rank() * NW + wid;
-    int *row = dense + (size_t)team * g.n;
-    SegTab &seg = segs[wid];
-    long long *pv = pvs[wid];
-    const int *glob_list = lists + 4 * (size_t)g.n;
-    const int nh = counters[CNT_C4_TEAM];
-    for (int h = team; h < nh; h += teams) {
-        const int u = glob_list[h];
-        const int4 ru = g.rinfo[u];
-        const int b = ru.x, din = ru.y - ru.x;
-        const int nch = (din + 31) >> 5;
-        // wedges per chunk (P[c]), then an exclusive scan in place: each
-        // thread owns a run of consecutive chunks, and only it touches them
-        for (int c = wid; c < nch; c += NW) {
-            const int p = c * 32 + lane;
-            const int l = p < din ? wedge_len(g, u, g.rinfo[g.ncol[b + p]]) : 0;
-            const int sum = warp_sum(l);
-            if (lane == 0) P[c] = sum;
+// Root order of the key-tiled tier: the queued roots (list 4, their wedge
+// counts in list 1) sorted by decreasing wedge count (64 buckets, two per
+// octave) into list 0, and the prefix sums of their in-degrees (the offsets
+// of their cursors) into list 2. One CTA.
+__global__ void __launch_bounds__(1024) k_c4_tiled_plan(Graph g, int *lists, int *counters) {
+    __shared__ int hist[64], base[64];
+    __shared__ int wsum[32];
+    if (degree_overflow(counters)) return;
+    const int nt = counters[CNT_C4_TEAM];
+    if (nt == 0) return;
+    const int *roots = lists + 4 * (size_t)g.n, *wts = lists + (size_t)g.n;
+    int *sorted = lists, *offs = lists + 2 * (size_t)g.n;
+    auto bucket = [](int w) {
+        const int e = 31 - __clz(max(w, 1));
+        const int half = e > 0 ? (w >> (e - 1)) & 1 : 0;
+        return 63 - min(63, 2 * e + half);
+    };
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) atomicAdd(&hist[bucket(wts[i])], 1);
+    __syncthreads();
+    if (threadIdx.x < 32) {   // exclusive scan of 64 buckets, two per lane
+        const int a = hist[2 * threadIdx.x], b = hist[2 * threadIdx.x + 1];
+        const int ex = warp_inclusive_scan(a + b) - (a + b);
+        base[2 * threadIdx.x] = ex;
+        base[2 * threadIdx.x + 1] = ex + a;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) sorted[atomicAdd(&base[bucket(wts[i])], 1)] = roots[i];
+    __syncthreads();
+    int carry = 0;
+    for (int j0 = 0; j0 < nt; j0 += blockDim.x) {
+        const int j = j0 + threadIdx.x;
+        int din = 0;
+        if (j < nt) {
+            const int4 r = g.rinfo[sorted[j]];
+            din = r.y - r.x;
         }
+        const int incl = warp_inclusive_scan(din);
+        if (lane_id() == 31) wsum[threadIdx.x >> 5] = incl;
         __syncthreads();
-        {
-            const int per = (nch + CT_THREADS - 1) / CT_THREADS;
-            const int c0 = min(threadIdx.x * per, nch), c1 = min(c0 + per, nch);
-            int run = 0;
-            for (int c = c0; c < c1; ++c) run += P[c];
-            const int incl = warp_inclusive_scan(run);
-            if (lane == 31) wsum[wid] = incl;
-            __syncthreads();
-            if (wid == 0) {
-                const int x = wsum[lane];
-                wsum[lane] = warp_inclusive_scan(x) - x;
-            }
-            __syncthreads();
-            int acc = wsum[wid] + incl - run;
-            for (int c = c0; c < c1; ++c) {
-                const int t = P[c];
-                P[c] = acc;
-                acc += t;
-            }
-            if (c0 < c1 && c1 == nch) P[nch] = acc;   // W
-        }
+        if (threadIdx.x < 32) wsum[threadIdx.x] = warp_inclusive_scan(wsum[threadIdx.x]);
         __syncthreads();
-        const int W = P[nch];
-        const int lo = (int)((long long)W * slice / SLICES), hi = (int)((long long)W * (slice + 1) / SLICES);
-        // chunks overlapping [lo, hi): f(act, q, w) per wedge, done(v) per chunk
-        auto pass = [&](auto f, auto done) {
-            if (lo >= hi) return;
-            int c = 0, top = nch;   // last chunk with P[c] <= lo
-            while (top - c > 1) {
-                const int mid = (c + top) >> 1;
-                if (P[mid] <= lo) c = mid; else top = mid;
-            }
-            for (; c < nch && P[c] < hi; ++c) {
-                int v, len, pre;
-                const int total = wedge_chunk(g, u, b, din, c * 32, seg, v, len, pre);
-                const int from = max(lo - P[c], 0), to = min(hi - P[c], total);
-                seg_visit<4>(g.ncol, seg, pre, len, to, from, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
-                __syncwarp();
-                done(v);
-                __syncwarp();
-            }
-        };
-        // Roots with many wedges for their row (W > u / 16) read the counts
-        // back in a coalesced sweep of row[0, u) for the C(c, 2) credits and
-        // with plain loads for the middle sums, and clear the row with a
-        // coalesced sweep; others mark first visitors and clear per wedge.
-        const bool sweep = (long long)W * 16 > u;
-        const int gt = (int)cluster.block_rank() * CT_THREADS + threadIdx.x;
-        constexpr int GT = CT_CLUSTER * CT_THREADS;
-        pass([&](bool act, int, int w) { if (act) atomicAdd(&row[w], 1); }, [](int) {});
-        cluster.sync();
-        long long su = 0;
-        pv[lane] = 0;
-        __syncwarp();
-        auto flush = [&](int v) {
-            const long long x = pv[lane];
-            if (x) add64(&vacc[v].C4, x);
-            pv[lane] = 0;
-        };
-        if (sweep) {
-            for (int w = gt; w < u; w += GT) {
-                const int c = row[w];
-                if (c >= 2) {
-                    su += c2(c);
-                    add64(&vacc[w].C4, c2(c));
-                }
-            }
-            pass([&](bool act, int q, int w) { add_middle(pv, q, act ? row[w] : 0); }, flush);
-        } else pass(
-            [&](bool act, int q, int w) {
-                int c = 0;
-                if (act) {
-                    const int old = atomicOr(&row[w], (int)0x80000000);
-                    c = old & 0x7fffffff;
-                    if (old >= 0 && c >= 2) {   // first visitor of this key
-                        su += c2(c);
-                        add64(&vacc[w].C4, c2(c));
-                    }
-                }
-                add_middle(pv, q, c);   // lanes of one v add once
-            },
-            flush);
-        su = warp_sum(su);
-        if (lane == 0 && su) add64(&vacc[u].C4, su);
-        cluster.sync();
-        if (sweep) {
-            for (int w = gt; w < u; w += GT) row[w] = 0;
-        } else {
-            pass([&](bool act, int, int w) { if (act) row[w] = 0; }, [](int) {});
-        }
-        cluster.sync();
+        const int before = (threadIdx.x >= 32 ? wsum[(threadIdx.x >> 5) - 1] : 0) + incl - din;
+        if (j < nt) offs[j] = carry + before;
+        carry += wsum[31];
+        __syncthreads();
     }
 }
 
-// One dense row per cluster, as many clusters as the SMs hold, but no more
-// rows than about 200 MB (1.5 times the L2) hold: the rows' atomics then
-// mostly stay in L2. On R-MAT scale 22 (16.8 MB a row) 11 rows instead of
-// 19 take 9% off this tier; 5 rows, all in L2, leave too few SMs working
-// and take twice as long.
-int c4_team_rows(int num_sms, long long n) {
-    int t = num_sms / CT_CLUSTER;
-    const long long fit = 200000000ll / (4 * (n > 0 ? n : 1));
-    if (fit < t) t = (int)fit;
-    return t < 1 ? 1 : t;
+// First position p in [cur, end) with a[p] >= key, given a[cur] < key
+// (a ascending): doubling steps from cur, then a binary search.
+__device__ __forceinline__ int gallop(const int *__restrict__ a, int cur, int end, int key) {
+    int lo = cur, step = 1, hi = end;
+    for (;;) {
+        const int pr = lo + step;
+        if (pr >= end) break;
+        if (a[pr] >= key) {
+            hi = pr;
+            break;
+        }
+        lo = pr;
+        step <<= 1;
+    }
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+template <bool WIDE>
+struct TileCounts {
+    unsigned *c;
+    __device__ __forceinline__ void add(int k) const {
+        if (WIDE) atomicAdd(&c[k], 1u);
+        else atomicAdd(&c[k >> 1], 1u << ((k & 1) << 4));
+    }
+    __device__ __forceinline__ int get(int k) const {
+        return WIDE ? (int)c[k] : (int)((c[k >> 1] >> ((k & 1) << 4)) & 0xffffu);
+    }
+    static constexpr int keys_per_word = WIDE ? 1 : 2;
+};
+
+// One root of the key-tiled tier, the whole CTA. st: its cursors.
+template <bool WIDE>
+__device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u, int2 *st, unsigned *cnt,
+                                              SegTab *segs, long long *pvs, int *s_next) {
+    const int lane = lane_id(), wid = threadIdx.x >> 5;
+    const int4 ru = g.rinfo[u];
+    const int b = ru.x, din = ru.y - ru.x;
+    const int nch = (din + 31) >> 5;
+    constexpr int TK = CK_WORDS * TileCounts<WIDE>::keys_per_word;
+    const TileCounts<WIDE> T{cnt};
+    SegTab &seg = segs[wid];
+    long long *pv = pvs + wid * 32;
+    // Chunks of 32 in-neighbours: one warp each when there are enough, else
+    // every warp takes every chunk and a share of its windows.
+    const bool shared_chunks = nch < CK_NW;
+    const int c0 = shared_chunks ? 0 : wid, cstep = shared_chunks ? 1 : CK_NW;
+    const int wbase = shared_chunks ? wid * 32 : 0, wstride = shared_chunks ? CK_NW * 32 : 32;
+    // cursors: each in-neighbour v's wedge prefix [row start, position of u in N+(v))
+    int mn = CK_INF;
+    for (int p = threadIdx.x; p < din; p += CK_THREADS) {
+        const int v = g.ncol[b + p];
+        const int4 rv = g.rinfo[v];
+        const int e = lower_bound(g.ncol, rv.y, rv.z, u);
+        st[p] = make_int2(rv.x, e);
+        if (rv.x < e) mn = min(mn, g.ncol[rv.x]);
+    }
+    mn = -warp_max(-mn);
+    if (threadIdx.x == 0) *s_next = CK_INF;
+    __syncthreads();
+    if (lane == 0) atomicMin(s_next, mn);
+    for (int i = threadIdx.x; i < CK_NW * 32; i += CK_THREADS) pvs[i] = 0;
+    __syncthreads();
+    int lo = *s_next;
+    long long su = 0;
+    while (lo < u) {
+        const int hi = min(lo + TK, u);
+        const int nk = hi - lo;
+        // the run of in-neighbour p inside [lo, hi): [cur, cur + len)
+        auto run = [&](int p, int &v, int &cur, int &len, int &nxt, int &end) {
+            v = -1, cur = 0, len = 0, nxt = CK_INF, end = 0;
+            if (p < din) {
+                v = g.ncol[b + p];
+                const int2 ce = st[p];
+                cur = ce.x, end = ce.y;
+                if (cur < end) {
+                    nxt = g.ncol[cur];
+                    if (nxt < hi) len = gallop(g.ncol, cur, end, hi) - cur;
+                }
+            }
+        };
+        __syncthreads();
+        if (threadIdx.x == 0) *s_next = CK_INF;
+        // 1. count the tile's wedges
+        for (int c = c0; c < nch; c += cstep) {
+            int v, cur, len, nxt, end, pre;
+            run(c * 32 + lane, v, cur, len, nxt, end);
+            const int total = seg_build(seg, cur, len, pre);
+            if (total)
+                seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int, int, int w) {
+                    if (ok && (unsigned)(w - lo) < (unsigned)nk) T.add(w - lo);   // always, for a simple graph
+                });
+            __syncwarp();
+        }
+        __syncthreads();
+        // 2. C(c, 2) to every key with c >= 2 and to u (the counts are only read from here on)
+        const int nw4 = (nk + 4 * T.keys_per_word - 1) / (4 * T.keys_per_word);
+        for (int i = threadIdx.x; i < nw4; i += CK_THREADS) {
+            const uint4 q = reinterpret_cast<const uint4 *>(cnt)[i];
+            if (!(q.x | q.y | q.z | q.w)) continue;
+            const unsigned qw[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int h = 0; h < T.keys_per_word; ++h) {
+                    const int c = WIDE ? (int)qw[j] : (int)((qw[j] >> (16 * h)) & 0xffffu);
+                    if (c >= 2) {
+                        const int k = (4 * i + j) * T.keys_per_word + h;
+                        su += c2(c);
+                        add64(&vacc[lo + k].C4, c2(c));
+                    }
+                }
+            }
+        }
+        // 3. middle vertices: c - 1 per wedge, summed per in-neighbour
+        int tnext = CK_INF;
+        for (int c = c0; c < nch; c += cstep) {
+            const int p = c * 32 + lane;
+            int v, cur, len, nxt, end, pre;
+            run(p, v, cur, len, nxt, end);
+            const int total = seg_build(seg, cur, len, pre);
+            if (total)
+                seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int q, int, int w) {
+                    const bool in = ok && (unsigned)(w - lo) < (unsigned)nk;
+                    add_middle(shared_chunks ? pvs : pv, q, in ? T.get(w - lo) : 0);
+                });
+            if (shared_chunks) __syncthreads(); else __syncwarp();
+            if (!shared_chunks || wid == 0) {
+                long long *pm = shared_chunks ? pvs : pv;
+                const long long x = pm[lane];
+                if (x) add64(&vacc[v].C4, x);
+                pm[lane] = 0;
+                if (len > 0) {
+                    cur += len;
+                    st[p].x = cur;
+                    nxt = cur < end ? g.ncol[cur] : CK_INF;
+                }
+                tnext = min(tnext, nxt);
+            }
+            if (shared_chunks) __syncthreads(); else __syncwarp();
+        }
+        tnext = -warp_max(-tnext);
+        if (lane == 0 && tnext < CK_INF) atomicMin(s_next, tnext);
+        __syncthreads();
+        // 4. clear the tile
+        for (int i = threadIdx.x; i < nw4; i += CK_THREADS) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+        lo = *s_next;
+    }
+    su = warp_sum(su);
+    if (lane == 0 && su) add64(&vacc[u].C4, su);
+    __syncthreads();
+}
+
+// cursors: room for `cap` pairs; a list of roots whose in-degrees sum to
+// more (only for a CSR that is not symmetric) stops with ENOTSIMPLE.
+__global__ void __launch_bounds__(CK_THREADS) k_c4_tiled(Graph g, VAcc *vacc, const int *lists, int *counters,
+                                                         int2 *cursors, long long cap, int *status) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    unsigned *cnt = reinterpret_cast<unsigned *>(dsm);
+    SegTab *segs = reinterpret_cast<SegTab *>(cnt + CK_WORDS);
+    long long *pvs = reinterpret_cast<long long *>(segs + CK_NW);
+    int *s_next = reinterpret_cast<int *>(pvs + CK_NW * 32);
+    int *s_job = s_next + 1;
+    if (degree_overflow(counters)) return;
+    const int nt = counters[CNT_C4_TEAM];
+    if (nt == 0) return;
+    const int *sorted = lists, *offs = lists + 2 * (size_t)g.n;
+    for (int i = threadIdx.x; i < CK_WORDS / 4; i += CK_THREADS)
+        reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) *s_job = atomicAdd(&counters[CNT_C4_TILED_NEXT], 1);
+        __syncthreads();
+        const int j = *s_job;
+        if (j >= nt) break;
+        const int u = sorted[j];
+        const int4 ru = g.rinfo[u];
+        if ((long long)offs[j] + (ru.y - ru.x) > cap || offs[j] < 0) {
+            if (threadIdx.x == 0) set_status(status, ST_ENOTSIMPLE);
+            continue;
+        }
+        int2 *st = cursors + offs[j];
+        if (ru.y - ru.x <= CK_NARROW_MAXD) c4_tiled_root<false>(g, vacc, u, st, cnt, segs, pvs, s_next);
+        else c4_tiled_root<true>(g, vacc, u, st, cnt, segs, pvs, s_next);
+    }
 }
 
 // Count bits of a packed table for ids below n: the key takes bits(n - 1).
@@ -741,18 +848,20 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     // graphs, batches) that is below what the warp tier takes, and the warp
     // tier counts in split tables instead
     const bool packed = (1ll << cb) - 2 >= maxw;
+    const int teamw = w.tune[TUNE_C4_TEAM_MINW];
     if (packed)
         k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
-                                                                             cb);
+                                                                             cb, teamw);
     else
         k_c4_warp_split<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters,
-                                                                                   maxw, cb);
+                                                                                   maxw, cb, teamw);
     after_launch(st, K_C4_WARP);
     // roots k_c4_warp queued for the 8 KB tables: one resident wave
     if (packed)
-        k_c4_warp_big<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb);
+        k_c4_warp_big<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb, teamw);
     else
-        k_c4_warp_big_split<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb);
+        k_c4_warp_big_split<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb,
+                                                                     teamw);
     after_launch(st, K_C4_WARP_BIG);
     k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MIDP);
@@ -760,14 +869,12 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     after_launch(st, K_C4_MID);
     k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
-    if (w.c4slots > 0) {
-        const long long words = (long long)c4_dense_words(w.c4slots, w.n);
-        k_c4_zero_dense<<<w.num_sms * 4, 256, 0, st>>>(w.c4dense, words, w.counters);
-        after_launch(st, K_C4_ZERO);
-        k_c4_team<<<w.c4slots * CT_CLUSTER, CT_THREADS, CT_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
-                                                                       w.c4dense, w.c4slots);
-        after_launch(st, K_C4_TEAM);
-    }
+    k_c4_tiled_plan<<<1, 1024, 0, st>>>(g, w.lists, w.counters);
+    after_launch(st, K_C4_PLAN);
+    k_c4_tiled<<<w.num_sms, CK_THREADS, CK_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
+                                                      reinterpret_cast<int2 *>(w.tcnt), (long long)w.m / 2,
+                                                      w.status);
+    after_launch(st, K_C4_TILED);
 }
 
 void configure_cycle4() {
@@ -779,7 +886,7 @@ void configure_cycle4() {
     cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_midp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM);
-    cudaFuncSetAttribute(k_c4_team, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CT_SMEM);
+    cudaFuncSetAttribute(k_c4_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CK_SMEM);
 }
 
 }  // namespace niorca

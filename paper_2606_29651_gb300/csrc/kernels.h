@@ -23,11 +23,9 @@ struct Work {
     int *scan_part = nullptr;// scan block partials
     int *lists = nullptr;    // heavy-vertex lists, 6 x n
     int *counters = nullptr; // list lengths and flags, 16 ints
-    int *c4dense = nullptr;  // dense counting rows for the largest 4-cycle roots
-    int c4slots = 0;         // rows in c4dense (each n ints), one per team of CTAs
     int *status = nullptr;   // device status word (not part of the carve)
     int num_sms = 0;
-    int tune[8] = {16, 8, 8, 8, 8, 32, 1536, 64};  // see TuneIndex
+    int tune[11] = {16, 8, 8, 8, 8, 32, 1536, 64, 1152, 8192, 12288};  // see TuneIndex
     int induced = 0;         // write induced instead of non-induced counts
 };
 
@@ -42,21 +40,30 @@ enum TuneIndex {
     TUNE_LONG_ROW_CLASS = 5, // degree class from which a row is relabelled by a whole CTA
     TUNE_C4_WARP_MAXW = 6,   // largest wedge count W of a 4-cycle root kept in one warp (<= 1536)
     TUNE_WARP_MAXD = 7,      // largest out-degree of a triangle root kept in one warp (<= 64)
-    TUNE_COUNT = 8
+    TUNE_TRI_BITS_MAXD = 8,  // largest out-degree of a CTA-tier triangle root that keeps the bit matrix R (<= 1152)
+    TUNE_TRI_HASH_MAXD = 9,  // largest out-degree of a CTA-tier triangle root that hashes N+(u) (<= 8192)
+    TUNE_C4_TEAM_MINW = 10,  // 4-cycle roots with more wedges than this go to the key-tiled tier (<= 12288)
+    TUNE_COUNT = 11
 };
 
 // Indices into Work::counters.
 // The triangle and aggregate heavy lists hold two tiers each: CTA-sized
 // roots from the front (CNT_*_HEAVY), the largest from the back (CNT_*_BIG).
 enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_TEAM = 3, CNT_DMAX = 4, CNT_C4_MID = 5,
-       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8, CNT_C4_WBIG = 9 };
+       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8, CNT_C4_WBIG = 9, CNT_C4_TILED_NEXT = 10 };
+
+// Whether the degree pass found a degree above MAX_DEGREE. NIORCA_EOVERFLOW
+// is then recorded already, and every kernel after the relabelling returns
+// at once: their fixed-size shared buffers and 32-bit partial sums rely on
+// the bound (Sec. 3 bounds the work by the largest degree; the bound itself
+// is this library's choice, see MAX_DEGREE).
+__device__ __forceinline__ bool degree_overflow(const int *counters) {
+    return *reinterpret_cast<const volatile int *>(counters + CNT_DMAX) > MAX_DEGREE;
+}
 
 constexpr int RL_TILE = 2048;        // vertices per class-histogram tile
 constexpr int SCAN_TILE = 4096;      // elements per scan block
 constexpr int LONG_ROW_CLASS = 32;   // deg_class(512): rows from here on get a CTA each
-// Dense rows (one per cluster of CTAs) of the largest 4-cycle tier, n ints each.
-int c4_team_rows(int num_sms, long long n);
-inline size_t c4_dense_words(long long rows, long long n) { return (size_t)(rows * n); }
 
 size_t scan_partials(long long len);
 void launch_exclusive_scan(const int *in, int *out, long long len, bool write_total, int *part,
@@ -73,7 +80,7 @@ void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *st
 // Kernel ids for the optional per-kernel event timing and launch counting.
 enum KernelId {
     K_CLASS_HIST, K_SCAN, K_CLASS_SCATTER, K_RELABEL_WARP, K_RELABEL_CTA, K_BATCH_SETUP,
-    K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_ZERO, K_C4_TEAM,
+    K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_PLAN, K_C4_TILED,
     K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_C4_WARP_BIG, K_COUNT
 };
 const char *kernel_name(int id);

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -36,8 +37,8 @@ thread_local Timeline *t_cur = nullptr;
 
 const char *const kNames[K_COUNT] = {
     "k_class_hist", "k_scan", "k_class_scatter", "k_relabel_rows_warp", "k_relabel_rows_cta", "k_batch_setup",
-    "k_tri_warp", "k_tri_cta", "k_agg_warp", "k_agg_cta", "k_c4_warp", "k_c4_cta", "k_c4_zero_dense",
-    "k_c4_team", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big",
+    "k_tri_warp", "k_tri_cta", "k_agg_warp", "k_agg_cta", "k_c4_warp", "k_c4_cta", "k_c4_tiled_plan",
+    "k_c4_tiled", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big",
     "k_c4_warp_big"};
 }  // namespace
 
@@ -92,12 +93,21 @@ void timeline_collect() {
     g_pending.clear();
 }
 
+// Status words: one device int per stream that has called into the library
+// on this device, so that a call reports only into the word of the stream it
+// was enqueued on. The words come from one slab allocated with the device
+// state (no allocation later, e.g. inside stream capture); once every word
+// of the slab is taken, further streams share words by a hash of the handle.
+constexpr int STATUS_WORDS = 4096;
+
 struct DeviceState {
     bool ready = false;
     cudaMemPool_t pool = nullptr;
-    int *status = nullptr;
+    int *status_slab = nullptr;
+    int status_used = 0;
+    std::unordered_map<const void *, int> status_of;   // stream -> word index
     int num_sms = 0;
-    int tune[TUNE_COUNT] = {16, 8, 8, 8, 8, 32, 1536, 64};
+    int tune[TUNE_COUNT] = {16, 8, 8, 8, 8, 32, 1536, 64, 1152, 8192, 12288};
 };
 
 constexpr int MAX_DEVICES = 64;
@@ -119,8 +129,9 @@ niorca_status device_state(DeviceState **out) {
         if (cudaMemPoolCreate(&d.pool, &props) != cudaSuccess) return NIORCA_ECUDA;
         uint64_t keep = UINT64_MAX;
         cudaMemPoolSetAttribute(d.pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        if (cudaMalloc(&d.status, sizeof(int)) != cudaSuccess) return NIORCA_ENOMEM;
-        if (cudaMemset(d.status, 0, sizeof(int)) != cudaSuccess) return NIORCA_ECUDA;
+        if (cudaMalloc(&d.status_slab, sizeof(int) * STATUS_WORDS) != cudaSuccess) return NIORCA_ENOMEM;
+        if (cudaMemset(d.status_slab, 0, sizeof(int) * STATUS_WORDS) != cudaSuccess) return NIORCA_ECUDA;
+        if (cudaDeviceSynchronize() != cudaSuccess) return NIORCA_ECUDA;
         configure_stage1();
         configure_stage2();
         configure_cycle4();
@@ -131,20 +142,32 @@ niorca_status device_state(DeviceState **out) {
     return NIORCA_OK;
 }
 
+// The status word of `st` on this device (see STATUS_WORDS).
+int *status_word(DeviceState *ds, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const void *key = static_cast<const void *>(st);
+    auto it = ds->status_of.find(key);
+    if (it != ds->status_of.end()) return ds->status_slab + it->second;
+    if (ds->status_used < STATUS_WORDS) {
+        const int idx = ds->status_used++;
+        ds->status_of.emplace(key, idx);
+        return ds->status_slab + idx;
+    }
+    const uint64_t h = reinterpret_cast<uintptr_t>(key) * 0x9E3779B97F4A7C15ull;
+    return ds->status_slab + (h >> 40) % STATUS_WORDS;
+}
+
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t vinfo, perm, chist, coff, nrow, split, rinfo, ncol, tcnt, vacc, scan_part, lists, counters, c4dense, vrange;
+    size_t vinfo, perm, chist, coff, nrow, split, rinfo, ncol, tcnt, vacc, scan_part, lists, counters, vrange;
     size_t total;
-    int ntiles, c4slots;
+    int ntiles;
 };
 
 Layout plan(long long n, long long m, int num_sms, bool batch) {
     Layout L;
     L.ntiles = (int)((n + RL_TILE - 1) / RL_TILE);
-    // the dense 4-cycle rows are only reachable by a root with more than
-    // 12288 wedges, which needs m above that; one row per team of CTAs
-    L.c4slots = m > 12288 ? c4_team_rows(num_sms, n) : 0;
     const long long nt = L.ntiles;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + (bytes ? bytes : 1)); return at; };
@@ -162,7 +185,6 @@ Layout plan(long long n, long long m, int num_sms, bool batch) {
     L.scan_part = take(4 * (sp1 > sp2 ? sp1 : sp2));
     L.lists = take(4 * 6 * n);
     L.counters = take(4 * 16);
-    L.c4dense = take(4 * c4_dense_words(L.c4slots, n));
     L.vrange = batch ? take(8 * n) : 0;
     L.total = o;
     return L;
@@ -209,9 +231,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     w.scan_part = reinterpret_cast<int *>(b + L.scan_part);
     w.lists = reinterpret_cast<int *>(b + L.lists);
     w.counters = reinterpret_cast<int *>(b + L.counters);
-    w.c4dense = reinterpret_cast<int *>(b + L.c4dense);
-    w.c4slots = L.c4slots;
-    w.status = ds->status;
+    w.status = status_word(ds, st);
     w.num_sms = ds->num_sms;
     for (int i = 0; i < TUNE_COUNT; ++i) w.tune[i] = ds->tune[i];
     w.induced = induced;
@@ -219,7 +239,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     timeline_begin(st);
     if (batch) {
         int2 *vrange = reinterpret_cast<int2 *>(b + L.vrange);
-        launch_batch_setup(rowptr, vtx_offset, edge_offset, num_graphs, n, vrange, ds->status, ds->num_sms, st);
+        launch_batch_setup(rowptr, vtx_offset, edge_offset, num_graphs, n, vrange, w.status, ds->num_sms, st);
         launch_relabel_batch(rowptr, colidx, vrange, w, st);
     } else {
         launch_relabel(rowptr, colidx, w, st);
@@ -309,7 +329,8 @@ extern "C" niorca_status niorca_validate(const int32_t *rowptr, const int32_t *c
     DeviceState *ds = nullptr;
     niorca_status s = device_state(&ds);
     if (s != NIORCA_OK) return s;
-    launch_validate(rowptr, colidx, n, (int)m, ds->status, ds->num_sms, static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    launch_validate(rowptr, colidx, n, (int)m, status_word(ds, st), ds->num_sms, st);
     return check_launch();
 }
 
@@ -317,10 +338,13 @@ extern "C" niorca_status niorca_last_status(void *stream) {
     DeviceState *ds = nullptr;
     niorca_status s = device_state(&ds);
     if (s != NIORCA_OK) return s;
-    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return NIORCA_ECUDA;
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *word = status_word(ds, st);
     int bits = 0;
-    if (cudaMemcpy(&bits, ds->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return NIORCA_ECUDA;
-    if (bits && cudaMemset(ds->status, 0, sizeof(int)) != cudaSuccess) return NIORCA_ECUDA;
+    // read and clear in the stream's own order, then wait for both
+    if (cudaMemcpyAsync(&bits, word, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return NIORCA_ECUDA;
+    if (cudaMemsetAsync(word, 0, sizeof(int), st) != cudaSuccess) return NIORCA_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return NIORCA_ECUDA;
     const niorca_status order[] = {NIORCA_EINVAL, NIORCA_ENOTSIMPLE, NIORCA_EOVERFLOW, NIORCA_ETIMEOUT};
     for (niorca_status c : order)
         if (bits & (1 << c)) return c;
@@ -386,6 +410,9 @@ bool tune_valid(int i, int v) {
     case TUNE_LONG_ROW_CLASS: return v >= 1 && v < NCLASS;
     case TUNE_C4_WARP_MAXW: return v >= 2 && v <= 1536;
     case TUNE_WARP_MAXD: return v >= 2 && v <= 64;
+    case TUNE_TRI_BITS_MAXD: return v >= 2 && v <= 1152;
+    case TUNE_TRI_HASH_MAXD: return v >= 2 && v <= 8192;
+    case TUNE_C4_TEAM_MINW: return v >= 2 && v <= 12288;
     default: return v >= 1 && v <= 64;   // CTAs per SM
     }
 }

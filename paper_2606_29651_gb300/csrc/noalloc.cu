@@ -70,7 +70,7 @@ size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Carves the static array into the buffers of one call; returns the bytes
 // needed (which may exceed the array; the caller checks).
-size_t carve(unsigned char *base, long long n, long long m, int slots, Work *w) {
+size_t carve(unsigned char *base, long long n, long long m, Work *w) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
         unsigned char *p = base + o;
@@ -92,8 +92,6 @@ size_t carve(unsigned char *base, long long n, long long m, int slots, Work *w) 
     w->scan_part = reinterpret_cast<int *>(take(4 * (sp1 > sp2 ? sp1 : sp2)));
     w->lists = reinterpret_cast<int *>(take(4 * 6 * n));
     w->counters = reinterpret_cast<int *>(take(4 * 16));
-    w->c4dense = reinterpret_cast<int *>(take(4 * c4_dense_words(slots, n)));
-    w->c4slots = slots;
     w->ntiles = (int)nt;
     return o;
 }
@@ -111,15 +109,8 @@ extern "C" niorca_status niorca_count_noalloc(const int32_t *rowptr, const int32
     NoallocDevice *d = nullptr;
     niorca_status s = noalloc_setup(&d);
     if (s != NIORCA_OK) return s;
-    // Dense 4-cycle rows (one per CTA of the widest tier) only when a root can
-    // need them; fewer rows if the graph is otherwise near the limit.
     Work w;
-    int slots = m > 12288 ? 8 : 0;
-    size_t need = carve(d->scratch, n, m, slots, &w);
-    while (need > NIORCA_NOALLOC_SCRATCH_BYTES && slots > 1) {
-        slots /= 2;
-        need = carve(d->scratch, n, m, slots, &w);
-    }
+    const size_t need = carve(d->scratch, n, m, &w);
     if (need > NIORCA_NOALLOC_SCRATCH_BYTES) return NIORCA_ENOMEM;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     w.n = n;

@@ -97,8 +97,10 @@ constexpr int SOLVE_WARPS = 8;
 
 __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(Graph g, const VAcc *vacc, const int *perm,
                                                             const int2 *vinfo, long long *out, int induced,
-                                                            const int *coff, int ntiles, int long_class) {
+                                                            const int *coff, int ntiles, int long_class,
+                                                            const int *counters) {
     __shared__ long long obuf[SOLVE_WARPS][32 * 15];
+    if (degree_overflow(counters)) return;
     const int lane = lane_id();
     long long *ob = obuf[threadIdx.x >> 5];
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(Graph g, const VAcc 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], SOLVE_WARPS * 32, 0, st>>>(
-        g, w.vacc, w.perm, w.vinfo, out, w.induced, w.coff, w.ntiles, w.tune[TUNE_LONG_ROW_CLASS]);
+        g, w.vacc, w.perm, w.vinfo, out, w.induced, w.coff, w.ntiles, w.tune[TUNE_LONG_ROW_CLASS], w.counters);
     after_launch(st, K_SOLVE);
 }
 

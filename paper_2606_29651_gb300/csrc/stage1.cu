@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
+    if (degree_overflow(counters)) return;
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
@@ -167,9 +168,13 @@ __device__ __forceinline__ int out_index(const int *hk, const int *hv, unsigned 
 }
 
 // One CTA per root u of the list (roots list[0 .. count) or, with BACK,
-// list[n - 1], list[n - 2], ...).
+// list[n - 1], list[n - 2], ...). A root keeps the bit matrix R up to
+// bits_maxd and the hash of N+(u) up to hash_maxd (run-time limits no larger
+// than the compiled ones, bits_maxd <= hash_maxd), else it probes N+(u) by
+// binary search and enumerates the K4 of each triangle.
 template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK>
-__device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, const int *list, int count) {
+__device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, const int *list, int count,
+                                        int bits_maxd, int hash_maxd) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int TC_THREADS = THREADS;
     constexpr int NW = THREADS / 32;
@@ -178,8 +183,8 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
         const int u = BACK ? list[g.n - 1 - h] : list[h];
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
-        const bool use_bits = dp <= BITMAT_MAXD;
-        const bool use_hash = dp <= HASH_MAXD;
+        const bool use_hash = dp <= HASH_MAXD && dp <= hash_maxd;
+        const bool use_bits = use_hash && dp <= BITMAT_MAXD && dp <= bits_maxd;
         unsigned H = use_hash ? next_pow2(2 * dp) : 0;
         if (use_bits && H > (unsigned)BITMAT_HSLOTS) H = BITMAT_HSLOTS;
         const unsigned mask = H ? H - 1 : 0;
@@ -353,14 +358,18 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
 }
 
 __global__ void __launch_bounds__(TS_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters) {
-    tri_cta<TS_THREADS, TS_MAXD, 2 * TS_MAXD, TS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_TRI_HEAVY]);
+                                                        const int *counters, int bits_maxd, int hash_maxd) {
+    if (degree_overflow(counters)) return;
+    tri_cta<TS_THREADS, TS_MAXD, 2 * TS_MAXD, TS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_TRI_HEAVY],
+                                                            bits_maxd, hash_maxd);
 }
 
 __global__ void __launch_bounds__(TB_THREADS) k_tri_big(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters) {
+                                                        const int *counters, int bits_maxd, int hash_maxd) {
+    if (degree_overflow(counters)) return;
     tri_cta<TB_THREADS, TB_BITMAT_MAXD, TB_BITMAT_HSLOTS, TB_HASH_MAXD, true>(g, tcnt, vacc, heavy,
-                                                                            counters[CNT_TRI_BIG]);
+                                                                            counters[CNT_TRI_BIG], bits_maxd,
+                                                                            hash_maxd);
 }
 
 
@@ -370,9 +379,10 @@ void launch_stage1(Work &w, cudaStream_t st) {
     k_tri_warp<<<w.num_sms * w.tune[TUNE_GRID_TRI], TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
                                                                           maxd);
     after_launch(st, K_TRI_WARP);
-    k_tri_cta<<<w.num_sms * 6, TS_THREADS, TS_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    const int bits = w.tune[TUNE_TRI_BITS_MAXD], hash = w.tune[TUNE_TRI_HASH_MAXD];
+    k_tri_cta<<<w.num_sms * 6, TS_THREADS, TS_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
     after_launch(st, K_TRI_CTA);
-    k_tri_big<<<w.num_sms, TB_THREADS, TB_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters);
+    k_tri_big<<<w.num_sms, TB_THREADS, TB_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
     after_launch(st, K_TRI_BIG);
 }
 

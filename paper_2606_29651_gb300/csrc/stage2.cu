@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
+    if (degree_overflow(counters)) return;
     for (int u = gw; u < g.n; u += nw) {
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
@@ -141,7 +142,8 @@ constexpr size_t AB_SMEM = AB_SMEM_BITS > AB_SMEM_HASH ? AB_SMEM_BITS : AB_SMEM_
 static_assert(AB_SMEM <= 227 * 1024, "k_agg_big shared memory");
 
 template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK>
-__device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *vacc, const int *heavy, int nh) {
+__device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *vacc, const int *heavy, int nh,
+                                        int bits_maxd, int hash_maxd) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
     __shared__ int any_tri;
@@ -155,8 +157,8 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
         if (edge_aggregates(g, tcnt, vacc, u, s, dp, threadIdx.x, THREADS) && lane == 0) any_tri = 1;
         __syncthreads();
         if (!any_tri) continue;
-        const bool use_bits = dp <= BITMAT_MAXD;
-        const bool use_hash = dp <= HASH_MAXD;
+        const bool use_hash = dp <= HASH_MAXD && dp <= hash_maxd;
+        const bool use_bits = use_hash && dp <= BITMAT_MAXD && dp <= bits_maxd;
         unsigned H = use_hash ? next_pow2(2 * dp) : 0;
         if (use_bits && H > (unsigned)BITMAT_HSLOTS) H = BITMAT_HSLOTS;
         const unsigned mask = H ? H - 1 : 0;
@@ -270,14 +272,18 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
 }
 
 __global__ void __launch_bounds__(AS_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters) {
-    agg_cta<AS_THREADS, AS_MAXD, 2 * AS_MAXD, AS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY]);
+                                                        const int *counters, int bits_maxd, int hash_maxd) {
+    if (degree_overflow(counters)) return;
+    agg_cta<AS_THREADS, AS_MAXD, 2 * AS_MAXD, AS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY],
+                                                            bits_maxd, hash_maxd);
 }
 
 __global__ void __launch_bounds__(AB_THREADS) k_agg_big(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters) {
+                                                        const int *counters, int bits_maxd, int hash_maxd) {
+    if (degree_overflow(counters)) return;
     agg_cta<AB_THREADS, AB_BITMAT_MAXD, AB_BITMAT_HSLOTS, AB_HASH_MAXD, true>(g, tcnt, vacc, heavy,
-                                                                            counters[CNT_AGG_BIG]);
+                                                                            counters[CNT_AGG_BIG], bits_maxd,
+                                                                            hash_maxd);
 }
 
 void launch_stage2(Work &w, cudaStream_t st) {
@@ -287,9 +293,10 @@ void launch_stage2(Work &w, cudaStream_t st) {
     k_agg_warp<<<w.num_sms * w.tune[TUNE_GRID_AGG], AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters,
                                                                           maxd);
     after_launch(st, K_AGG_WARP);
-    k_agg_cta<<<w.num_sms * 6, AS_THREADS, AS_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    const int bits = w.tune[TUNE_TRI_BITS_MAXD], hash = w.tune[TUNE_TRI_HASH_MAXD];
+    k_agg_cta<<<w.num_sms * 6, AS_THREADS, AS_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
     after_launch(st, K_AGG_CTA);
-    k_agg_big<<<w.num_sms, AB_THREADS, AB_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters);
+    k_agg_big<<<w.num_sms, AB_THREADS, AB_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
     after_launch(st, K_AGG_BIG);
 }
 

@@ -11,7 +11,10 @@ submit() to the moment its counts are in host memory.
 
 The counts of a graph do not depend on which other graphs share its batch
 (the batched call counts the disjoint union, and no graphlet spans two
-components), so every result is identical alone and in the mix.
+components), so every result is identical alone and in the mix. Each batch
+reads the status word of its own stream. When a batch of several requests
+reports a malformed graph, its requests are queued again, each to run alone,
+so that only the malformed one fails.
 """
 from __future__ import annotations
 
@@ -28,7 +31,7 @@ from . import _lib
 
 
 class Request:
-    __slots__ = ("rowptr", "colidx", "n", "m", "future", "t_submit", "t_done")
+    __slots__ = ("rowptr", "colidx", "n", "m", "future", "t_submit", "t_done", "alone")
 
     def __init__(self, rowptr: np.ndarray, colidx: np.ndarray):
         self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
@@ -38,6 +41,7 @@ class Request:
         self.future: Future = Future()
         self.t_submit = time.perf_counter()
         self.t_done = None
+        self.alone = False   # run in a batch of its own (after its batch failed)
 
 
 def footprint(num_graphs: int, total_n: int, total_m: int) -> int:
@@ -141,6 +145,8 @@ class Server:
         take, n, m = [], 0, 0
         while self._pending and len(take) < self.max_batch_graphs:
             r = self._pending[0]
+            if take and (r.alone or take[0].alone):
+                break
             need = footprint(len(take) + 1, n + r.n, m + r.m)
             if take and (need > self.mem_budget - self._in_use or m + r.m > self.max_batch_edges):
                 break
@@ -233,6 +239,16 @@ class Server:
                 out[lo:hi] = res[lo:hi]
 
             self._ranges(unpack, total_n, 15 * total_n)
+        if err is not None and len(b.reqs) > 1 and err.status != _lib.Status.ECUDA:
+            # a malformed graph fails the whole batch: run each request alone
+            with self._cv:
+                for r in reversed(b.reqs):
+                    r.alone = True
+                    self._pending.appendleft(r)
+            self._in_use -= b.nbytes
+            self._free_slots.append(b.slot)
+            b.keep = None
+            return
         for g, r in enumerate(b.reqs):
             r.t_done = now
             if err is not None:

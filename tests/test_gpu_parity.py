@@ -220,3 +220,68 @@ def test_induced_counts_vs_definition(ni, name, make):
     out = ni.count_induced(torch.from_numpy(rp).to(dev), torch.from_numpy(ci).to(dev))
     ni.check()
     assert_same(out.cpu().numpy(), oracle.induced_count(rp, ci), name)
+
+
+def test_degree_above_bound_stops_with_eoverflow(ni):
+    # A star with 2^20 + 1 leaves: its centre's degree is above the bound
+    # under which every count and intermediate fits int64, so the degree pass
+    # records EOVERFLOW and every later stage returns without running.
+    from paper_2606_29651_gb300 import Status
+    k = (1 << 20) + 1
+    rp = np.zeros(k + 2, np.int64)
+    rp[1] = k
+    rp[2:] = k + np.arange(1, k + 1)
+    ci = np.concatenate([np.arange(1, k + 1), np.zeros(k, np.int64)]).astype(np.int32)
+    _expect_status(ni, rp.astype(np.int32), ci, Status.EOVERFLOW)
+    # exactly at the bound it counts, and the same stream reports OK again
+    k = 1 << 20
+    rp = np.zeros(k + 2, np.int64)
+    rp[1] = k
+    rp[2:] = k + np.arange(1, k + 1)
+    ci = np.concatenate([np.arange(1, k + 1), np.zeros(k, np.int64)]).astype(np.int32)
+    got = gpu_count(ni, rp.astype(np.int32), ci)
+    exp_centre = [k, 0, k * (k - 1) // 2, 0, 0, 0, 0, k * (k - 1) * (k - 2) // 6, 0, 0, 0, 0, 0, 0, 0]
+    assert got[0].tolist() == exp_centre
+    assert got[1].tolist() == [1, k - 1, 0, 0, 0, 0, (k - 1) * (k - 2) // 2, 0, 0, 0, 0, 0, 0, 0, 0]
+    assert (got[2:] == got[1]).all()
+
+
+@pytest.fixture
+def tuning(ni):
+    saved = ni.get_tuning()
+    yield ni
+    ni.set_tuning(**saved)
+
+
+@pytest.mark.parametrize("name,make", [
+    ("er_dense", lambda: gg.er(600, 0.5, 6)),
+    ("rmat14", lambda: gg.rmat(14, 16, seed=4)),
+    ("chunglu20k", lambda: gg.chunglu(20000, 2.2, 12.0, 5)),
+])
+def test_cta_tier_paths_at_low_thresholds(tuning, name, make):
+    # With low routing limits the CTA tiers of the triangle and aggregate
+    # stages meet roots of every kind on small graphs: bit matrix (out-degree
+    # <= 24), shared hash without the bit matrix (<= 48), and binary searches
+    # of N+(u) with a K4 enumeration per triangle beyond.
+    rp, ci = make()
+    exp = oracle.count(rp, ci)
+    tuning.set_tuning(warp_maxd=4, tri_bits_maxd=24, tri_hash_maxd=48)
+    assert_same(gpu_count(tuning, rp, ci), exp, name + " low limits")
+    tuning.set_tuning(warp_maxd=2, tri_bits_maxd=2, tri_hash_maxd=2)
+    assert_same(gpu_count(tuning, rp, ci), exp, name + " binary searches only")
+
+
+@pytest.mark.parametrize("name,make", [
+    ("rmat12", lambda: gg.rmat(12, 16, seed=3)),
+    ("er_dense", lambda: gg.er(600, 0.5, 6)),
+    ("chunglu20k", lambda: gg.chunglu(20000, 2.2, 12.0, 5)),
+    ("k3_900", lambda: gg.complete_bipartite(3, 900)),
+])
+def test_key_tiled_four_cycle_tier_for_every_root(tuning, name, make):
+    # Every root with more than two wedges goes to the widest 4-cycle tier.
+    rp, ci = make()
+    exp = oracle.count(rp, ci)
+    tuning.set_tuning(c4_warp_maxw=2, c4_team_minw=2)
+    assert_same(gpu_count(tuning, rp, ci), exp, name + " all roots in the widest tier")
+    tuning.set_tuning(c4_warp_maxw=300, c4_team_minw=600)
+    assert_same(gpu_count(tuning, rp, ci), exp, name + " mixed tiers")

@@ -37,8 +37,9 @@ def test_induced_c4_and_chordless_graphs():
 
 
 def test_printed_induced_equations():
-    """P:339 psi'13 = f13/2 - 3 psi14; P:344 psi'11 = (f11 - f13)/2 + 3 psi14;
-    P:349 psi'10 = f10 - f13 + 6 psi14, with the non-induced f* read back from
+    """The induced equations printed in Sec. 5: psi'13 = f13/2 - 3 psi14;
+    psi'11 = (f11 - f13)/2 + 3 psi14; psi'10 = f10 - f13 + 6 psi14, with
+    the non-induced f* read back from
     Eqs. o13, o12, o11, o10: f13 = 2 psi13, f12 = psi12, f11 = 2 psi11 - f13,
     f10 = psi10 - 2 psi12."""
     for rp, ci in (gg.er(300, 0.1, 2), gg.rmat(9, 16, seed=4), gg.er(60, 0.5, 5)):

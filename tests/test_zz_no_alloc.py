@@ -74,10 +74,31 @@ def test_noalloc_without_status_and_after_another_graph(lib):
     assert np.array_equal(_run(lib, "noalloc", *a), ra)
 
 
+def _scratch_bytes():
+    """NIORCA_NOALLOC_SCRATCH_BYTES as include/niorca.h defines it."""
+    import os
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "niorca.h")
+    mt = re.search(r"#define NIORCA_NOALLOC_SCRATCH_BYTES \(\(size_t\)(\d+) << (\d+)\)", open(hdr).read())
+    assert mt, "NIORCA_NOALLOC_SCRATCH_BYTES not found in niorca.h"
+    return int(mt.group(1)) << int(mt.group(2))
+
+
 def test_noalloc_rejects_a_graph_beyond_the_static_array(lib):
+    # The sizes claim a graph whose column array alone (4 m bytes, twice over
+    # in the work memory) is larger than the static array, so the call must
+    # refuse it on the host before anything is enqueued; the 8-element
+    # buffers are never read. Should the array ever grow past what such a
+    # graph needs, the test skips rather than pass undersized buffers.
+    scratch = _scratch_bytes()
+    n, m = 1_000_000, min(scratch // 2, 2**31 - 2)
+    lib.niorca_workspace_bytes.restype = ctypes.c_size_t
+    lib.niorca_workspace_bytes.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    need = lib.niorca_workspace_bytes(n, m)
+    if 8 * m <= 2 * scratch or need <= 2 * scratch:
+        pytest.skip("the static array is too large for this refusal check")
     small = torch.zeros(8, dtype=torch.int32, device="cuda:0")
     out = torch.zeros(8, dtype=torch.int64, device="cuda:0")
-    # n = 1e6, m = 3.2e7 needs ~0.4 GB of work memory: refused before any launch
-    rc = lib.niorca_count_noalloc(small.data_ptr(), small.data_ptr(), 1_000_000, 32_000_000, out.data_ptr(), None,
+    rc = lib.niorca_count_noalloc(small.data_ptr(), small.data_ptr(), n, m, out.data_ptr(), None,
                                   torch.cuda.current_stream().cuda_stream)
     assert rc == 4   # NIORCA_ENOMEM
