@@ -575,21 +575,24 @@ __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, cons
 // many keys, above). A root's wedges through its in-neighbour v are the
 // entries of row v below u, ascending, so the wedges that fall into a tile
 // are a run of that row: every in-neighbour keeps a cursor (the start of its
-// next run) and the end of its wedge prefix, and a tile's run is found by a
-// galloping search from the cursor. Each tile takes three steps: count its
-// wedges, credit C(c, 2) to every key w and to u from the counts, walk the
-// runs again adding c - 1 per wedge to its middle vertex, then clear. The
-// next tile starts at the smallest key any cursor points at, so key ranges
-// without wedges are skipped.
+// next run), the end of its wedge prefix and the key at the cursor. A tile
+// first finds every in-neighbour's run (a galloping search from the cursor,
+// one thread per in-neighbour) and marks the chunks of 32 in-neighbours that
+// have one; then it counts the runs' wedges, credits C(c, 2) to every key w
+// and to u from the counts, walks the runs again adding c - 1 per wedge to
+// its middle vertex, and clears. The next tile starts at the smallest key
+// any cursor points at, so key ranges without wedges are skipped.
 // The cursors of all these roots (their in-degrees sum to at most |E|) live
-// in the per-edge triangle counts, which nothing reads after the aggregate
-// stage: two ints per in-neighbour, |E| pairs in m ints.
+// in the region of the per-edge triangle counts, which nothing reads after
+// the aggregate stage and which is sized 8 m bytes for them: 16 bytes per
+// in-neighbour, |E| = m / 2 of them.
 constexpr int CK_THREADS = 1024;
 constexpr int CK_NW = CK_THREADS / 32;
 constexpr int CK_WORDS = 48 * 1024;                 // counter words in shared memory (192 KB)
 constexpr int CK_NARROW_MAXD = 65534;               // in-degree up to which 16-bit counters cannot overflow
 constexpr int CK_INF = 0x7fffffff;
-constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + 64;
+constexpr int CK_CBITS = (MAX_DEGREE / 32 + 31) / 32;  // words of chunk bits: in-degree <= MAX_DEGREE
+constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + CK_CBITS * 4 + 64;
 static_assert(CK_SMEM <= 227 * 1024, "k_c4_tiled shared memory");
 
 // Root order of the key-tiled tier: the queued roots (list 4, their wedge
@@ -676,14 +679,17 @@ struct TileCounts {
     static constexpr int keys_per_word = WIDE ? 1 : 2;
 };
 
-// One root of the key-tiled tier, the whole CTA. st: its cursors.
+// One root of the key-tiled tier, the whole CTA. st: one int4 per
+// in-neighbour {cursor, end of its wedge prefix, run length in the current
+// tile, key at the cursor}; the run length is 0 outside a tile's passes.
+// cbits: one bit per chunk of 32 in-neighbours with a run in the tile.
 template <bool WIDE>
-__device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u, int2 *st, unsigned *cnt,
-                                              SegTab *segs, long long *pvs, int *s_next) {
+__device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u, int4 *st, unsigned *cnt,
+                                              SegTab *segs, long long *pvs, unsigned *cbits, int *s_next) {
     const int lane = lane_id(), wid = threadIdx.x >> 5;
     const int4 ru = g.rinfo[u];
     const int b = ru.x, din = ru.y - ru.x;
-    const int nch = (din + 31) >> 5;
+    const int nch = (din + 31) >> 5, nbw = (nch + 31) >> 5;
     constexpr int TK = CK_WORDS * TileCounts<WIDE>::keys_per_word;
     const TileCounts<WIDE> T{cnt};
     SegTab &seg = segs[wid];
@@ -693,50 +699,57 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
     const bool shared_chunks = nch < CK_NW;
     const int c0 = shared_chunks ? 0 : wid, cstep = shared_chunks ? 1 : CK_NW;
     const int wbase = shared_chunks ? wid * 32 : 0, wstride = shared_chunks ? CK_NW * 32 : 32;
+    auto has_run = [&](int c) { return (cbits[c >> 5] >> (c & 31)) & 1u; };
     // cursors: each in-neighbour v's wedge prefix [row start, position of u in N+(v))
     int mn = CK_INF;
     for (int p = threadIdx.x; p < din; p += CK_THREADS) {
         const int v = g.ncol[b + p];
         const int4 rv = g.rinfo[v];
         const int e = lower_bound(g.ncol, rv.y, rv.z, u);
-        st[p] = make_int2(rv.x, e);
-        if (rv.x < e) mn = min(mn, g.ncol[rv.x]);
+        const int nx = rv.x < e ? g.ncol[rv.x] : CK_INF;
+        st[p] = make_int4(rv.x, e, 0, nx);
+        mn = min(mn, nx);
     }
     mn = -warp_max(-mn);
     if (threadIdx.x == 0) *s_next = CK_INF;
+    for (int i = threadIdx.x; i < CK_NW * 32; i += CK_THREADS) pvs[i] = 0;
+    for (int i = threadIdx.x; i < nbw; i += CK_THREADS) cbits[i] = 0;
     __syncthreads();
     if (lane == 0) atomicMin(s_next, mn);
-    for (int i = threadIdx.x; i < CK_NW * 32; i += CK_THREADS) pvs[i] = 0;
     __syncthreads();
     int lo = *s_next;
     long long su = 0;
     while (lo < u) {
         const int hi = min(lo + TK, u);
         const int nk = hi - lo;
-        // the run of in-neighbour p inside [lo, hi): [cur, cur + len)
-        auto run = [&](int p, int &v, int &cur, int &len, int &nxt, int &end) {
-            v = -1, cur = 0, len = 0, nxt = CK_INF, end = 0;
-            if (p < din) {
-                v = g.ncol[b + p];
-                const int2 ce = st[p];
-                cur = ce.x, end = ce.y;
-                if (cur < end) {
-                    nxt = g.ncol[cur];
-                    if (nxt < hi) len = gallop(g.ncol, cur, end, hi) - cur;
-                }
-            }
-        };
         __syncthreads();
         if (threadIdx.x == 0) *s_next = CK_INF;
+        // A. the run of every in-neighbour inside [lo, hi), one thread each;
+        // the next key of those without one bounds the next tile
+        int tnext = CK_INF;
+        for (int p = threadIdx.x; p < din; p += CK_THREADS) {
+            const int4 s4 = st[p];
+            if (s4.w < hi) {
+                st[p].z = gallop(g.ncol, s4.x, s4.y, hi) - s4.x;
+                atomicOr(&cbits[p >> 10], 1u << ((p >> 5) & 31));
+            } else {
+                tnext = min(tnext, s4.w);
+            }
+        }
+        __syncthreads();
         // 1. count the tile's wedges
         for (int c = c0; c < nch; c += cstep) {
-            int v, cur, len, nxt, end, pre;
-            run(c * 32 + lane, v, cur, len, nxt, end);
+            if (!has_run(c)) continue;
+            const int p = c * 32 + lane;
+            int cur = 0, len = 0, pre;
+            if (p < din) {
+                const int4 s4 = st[p];
+                cur = s4.x, len = s4.z;
+            }
             const int total = seg_build(seg, cur, len, pre);
-            if (total)
-                seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int, int, int w) {
-                    if (ok && (unsigned)(w - lo) < (unsigned)nk) T.add(w - lo);   // always, for a simple graph
-                });
+            seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int, int, int w) {
+                if (ok && (unsigned)(w - lo) < (unsigned)nk) T.add(w - lo);   // always, for a simple graph
+            });
             __syncwarp();
         }
         __syncthreads();
@@ -759,18 +772,22 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
                 }
             }
         }
-        // 3. middle vertices: c - 1 per wedge, summed per in-neighbour
-        int tnext = CK_INF;
+        // 3. middle vertices: c - 1 per wedge, summed per in-neighbour; the
+        // cursors move past the runs
         for (int c = c0; c < nch; c += cstep) {
+            if (!has_run(c)) continue;
             const int p = c * 32 + lane;
-            int v, cur, len, nxt, end, pre;
-            run(p, v, cur, len, nxt, end);
+            int v = -1, cur = 0, len = 0, end = 0, pre;
+            if (p < din) {
+                v = g.ncol[b + p];
+                const int4 s4 = st[p];
+                cur = s4.x, end = s4.y, len = s4.z;
+            }
             const int total = seg_build(seg, cur, len, pre);
-            if (total)
-                seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int q, int, int w) {
-                    const bool in = ok && (unsigned)(w - lo) < (unsigned)nk;
-                    add_middle(shared_chunks ? pvs : pv, q, in ? T.get(w - lo) : 0);
-                });
+            seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int q, int, int w) {
+                const bool in = ok && (unsigned)(w - lo) < (unsigned)nk;
+                add_middle(shared_chunks ? pvs : pv, q, in ? T.get(w - lo) : 0);
+            });
             if (shared_chunks) __syncthreads(); else __syncwarp();
             if (!shared_chunks || wid == 0) {
                 long long *pm = shared_chunks ? pvs : pv;
@@ -779,18 +796,19 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
                 pm[lane] = 0;
                 if (len > 0) {
                     cur += len;
-                    st[p].x = cur;
-                    nxt = cur < end ? g.ncol[cur] : CK_INF;
+                    const int nx = cur < end ? g.ncol[cur] : CK_INF;
+                    st[p] = make_int4(cur, end, 0, nx);
+                    tnext = min(tnext, nx);
                 }
-                tnext = min(tnext, nxt);
             }
             if (shared_chunks) __syncthreads(); else __syncwarp();
         }
         tnext = -warp_max(-tnext);
         if (lane == 0 && tnext < CK_INF) atomicMin(s_next, tnext);
         __syncthreads();
-        // 4. clear the tile
+        // 4. clear the tile and the chunk bits
         for (int i = threadIdx.x; i < nw4; i += CK_THREADS) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < nbw; i += CK_THREADS) cbits[i] = 0;
         lo = *s_next;
     }
     su = warp_sum(su);
@@ -798,15 +816,16 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
     __syncthreads();
 }
 
-// cursors: room for `cap` pairs; a list of roots whose in-degrees sum to
+// cursors: room for `cap` entries; a list of roots whose in-degrees sum to
 // more (only for a CSR that is not symmetric) stops with ENOTSIMPLE.
 __global__ void __launch_bounds__(CK_THREADS) k_c4_tiled(Graph g, VAcc *vacc, const int *lists, int *counters,
-                                                         int2 *cursors, long long cap, int *status) {
+                                                         int4 *cursors, long long cap, int *status) {
     extern __shared__ __align__(16) unsigned char dsm[];
     unsigned *cnt = reinterpret_cast<unsigned *>(dsm);
     SegTab *segs = reinterpret_cast<SegTab *>(cnt + CK_WORDS);
     long long *pvs = reinterpret_cast<long long *>(segs + CK_NW);
-    int *s_next = reinterpret_cast<int *>(pvs + CK_NW * 32);
+    unsigned *cbits = reinterpret_cast<unsigned *>(pvs + CK_NW * 32);
+    int *s_next = reinterpret_cast<int *>(cbits + CK_CBITS);
     int *s_job = s_next + 1;
     if (degree_overflow(counters)) return;
     const int nt = counters[CNT_C4_TEAM];
@@ -826,9 +845,9 @@ __global__ void __launch_bounds__(CK_THREADS) k_c4_tiled(Graph g, VAcc *vacc, co
             if (threadIdx.x == 0) set_status(status, ST_ENOTSIMPLE);
             continue;
         }
-        int2 *st = cursors + offs[j];
-        if (ru.y - ru.x <= CK_NARROW_MAXD) c4_tiled_root<false>(g, vacc, u, st, cnt, segs, pvs, s_next);
-        else c4_tiled_root<true>(g, vacc, u, st, cnt, segs, pvs, s_next);
+        int4 *st = cursors + offs[j];
+        if (ru.y - ru.x <= CK_NARROW_MAXD) c4_tiled_root<false>(g, vacc, u, st, cnt, segs, pvs, cbits, s_next);
+        else c4_tiled_root<true>(g, vacc, u, st, cnt, segs, pvs, cbits, s_next);
     }
 }
 
@@ -872,7 +891,7 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     k_c4_tiled_plan<<<1, 1024, 0, st>>>(g, w.lists, w.counters);
     after_launch(st, K_C4_PLAN);
     k_c4_tiled<<<w.num_sms, CK_THREADS, CK_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
-                                                      reinterpret_cast<int2 *>(w.tcnt), (long long)w.m / 2,
+                                                      reinterpret_cast<int4 *>(w.tcnt), (long long)w.m / 2,
                                                       w.status);
     after_launch(st, K_C4_TILED);
 }

@@ -18,7 +18,7 @@ struct Work {
     int *split = nullptr;    // scan input: degree of each new id
     int4 *rinfo = nullptr;   // {row start, split, row end, 0} per new id
     int *ncol = nullptr;     // relabelled neighbours, m
-    int *tcnt = nullptr;     // triangle count of each out-entry (u, v), u < v; m
+    int *tcnt = nullptr;     // triangle count of each out-entry (u, v), u < v; m ints in a region of 8 m bytes
     VAcc *vacc = nullptr;    // per-vertex accumulators, n
     int *scan_part = nullptr;// scan block partials
     int *lists = nullptr;    // heavy-vertex lists, 6 x n

@@ -179,7 +179,7 @@ Layout plan(long long n, long long m, int num_sms, bool batch) {
     L.split = take(4 * n);
     L.rinfo = take(16 * n);
     L.ncol = take(4 * m);
-    L.tcnt = take(4 * m);
+    L.tcnt = take(8 * m);   // 4 m for the per-edge triangle counts; 8 m for the cursors of the 4-cycle tiles
     L.vacc = take(sizeof(VAcc) * n);
     const size_t sp1 = scan_partials(NCLASS * nt), sp2 = scan_partials(n);
     L.scan_part = take(4 * (sp1 > sp2 ? sp1 : sp2));

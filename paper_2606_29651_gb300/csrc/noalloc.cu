@@ -86,7 +86,7 @@ size_t carve(unsigned char *base, long long n, long long m, Work *w) {
     w->split = reinterpret_cast<int *>(take(4 * n));
     w->rinfo = reinterpret_cast<int4 *>(take(16 * n));
     w->ncol = reinterpret_cast<int *>(take(4 * m));
-    w->tcnt = reinterpret_cast<int *>(take(4 * m));
+    w->tcnt = reinterpret_cast<int *>(take(8 * m));   // also the cursors of the key-tiled 4-cycle tier
     w->vacc = reinterpret_cast<VAcc *>(take(sizeof(VAcc) * n));
     const size_t sp1 = scan_partials(NCLASS * nt), sp2 = scan_partials(n);
     w->scan_part = reinterpret_cast<int *>(take(4 * (sp1 > sp2 ? sp1 : sp2)));
