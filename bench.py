@@ -216,6 +216,7 @@ def algorithmic_bytes(rowptr: np.ndarray, colidx: np.ndarray, c4_warp_ub: int = 
                   "k_relabel_rows_warp": 2 * res["B_csr"], "k_solve": res["B_csr"] + res["B_out"]}
     for k, msk in sh.c4_tiers(c4_warp_ub).items():
         per_kernel[k] = 4 * int(sh.w_root[msk].sum())
+    per_kernel["k_c4_mid"] += per_kernel.pop("k_c4_midp")   # one kernel takes both 128-thread queues
     res["per_kernel"] = per_kernel
     return res
 

@@ -46,6 +46,7 @@ struct __align__(16) VAcc {
 };
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -222,6 +223,9 @@ struct Graph {
     int m;              // CSR entries (2|E|)
     const int4 *rinfo;  // row bounds of every relabelled vertex
     const int *ncol;    // relabelled neighbours, rows ascending
+    const int2 *wl = nullptr;  // 4-cycle stage: at the position of in-neighbour v in row u (rows with at most
+                               // WL_MAXD in-neighbours), {start of row v, number of entries of row v below u}
 };
+constexpr int WL_MAXD = 1024;
 
 }  // namespace niorca

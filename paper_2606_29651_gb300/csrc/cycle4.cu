@@ -14,7 +14,7 @@
 // ending at the position of u, which a search of N+(v) finds. Roots are
 // routed by their wedge count W (a count is at most W too): one warp with a
 // 6 KB table (k_c4_warp) or an 8 KB one (k_c4_warp_big), four warps
-// (k_c4_midp / k_c4_mid), a 512-thread CTA (k_c4_cta), or, for the largest
+// (k_c4_mid, packed or split tables), a 512-thread CTA (k_c4_cta), or, for the largest
 // roots, a 1024-thread CTA that counts the root's key range tile by tile in
 // shared memory (k_c4_tiled). The other tables are open-addressing hash
 // tables in shared memory, either split (key and count arrays) or packed
@@ -61,6 +61,33 @@ __device__ __forceinline__ int wedge_len(const Graph &g, int u, const int4 &rv) 
     return lower_bound(g.ncol, rv.y, rv.z, u) - rv.x;
 }
 
+// The wedge segment {row start, length} of the in-neighbour at position p of
+// row u (din = u's in-degree): from the table k_c4_wedge_len filled, for the
+// rows it covers, else by a search of N+(v).
+__device__ __forceinline__ int2 wedge_seg(const Graph &g, int u, int din, int p) {
+    if (din <= WL_MAXD) return g.wl[p];
+    const int4 rv = g.rinfo[g.ncol[p]];
+    return make_int2(rv.x, wedge_len(g, u, rv));
+}
+
+// The wedge segment of every in-entry of the rows with at most WL_MAXD
+// in-neighbours, a half-warp per row: the row gather and binary search of
+// each entry, made here with every thread independent, so that the
+// per-root kernels read one coalesced 8-byte entry per in-neighbour.
+__global__ void __launch_bounds__(256, 8) k_c4_wedge_len(Graph g, int2 *wl, const int *counters) {
+    if (degree_overflow(counters)) return;
+    const int hl = threadIdx.x & 15;
+    const int gh = (blockIdx.x * blockDim.x + threadIdx.x) >> 4, nh = (gridDim.x * blockDim.x) >> 4;
+    for (int u = gh; u < g.n; u += nh) {
+        const int4 ru = g.rinfo[u];
+        if (ru.y - ru.x > WL_MAXD) continue;
+        for (int p = ru.x + hl; p < ru.y; p += 16) {
+            const int4 rv = g.rinfo[g.ncol[p]];
+            wl[p] = make_int2(rv.x, wedge_len(g, u, rv));
+        }
+    }
+}
+
 // Segment table of in-neighbour chunk cb of root u in the calling warp: the
 // wedge prefixes of the rows of v = ncol[b + cb + lane] concatenated. Returns
 // the total length; the lane's own v, segment length and offset come back in
@@ -73,9 +100,9 @@ __device__ __forceinline__ int wedge_chunk(const Graph &g, int u, int b, int din
     len = 0;
     if (p < din) {
         v = g.ncol[b + p];
-        const int4 rv = g.rinfo[v];
-        st = rv.x;
-        len = wedge_len(g, u, rv);
+        const int2 sl = wedge_seg(g, u, din, b + p);
+        st = sl.x;
+        len = sl.y;
     }
     return seg_build(T, st, len, pre);
 }
@@ -406,26 +433,23 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
     int un = i + nw < count ? root(i + nw) : 0;
     int4 ru = i < count ? g.rinfo[u] : Z;
     int4 ru1 = i + nw < count ? g.rinfo[un] : Z;
-    int v0 = (i < count && lane < ru.y - ru.x) ? g.ncol[ru.x + lane] : -1;
-    int4 rv0 = v0 >= 0 ? g.rinfo[v0] : Z;
+    const int2 Z2 = make_int2(0, 0);
+    // wedge segment through in-neighbour `lane` of the current root
+    int2 s0 = (i < count && lane < ru.y - ru.x && ru.y - ru.x <= 64) ? g.wl[ru.x + lane] : Z2;
     for (; i < count; i += nw) {
         const int i2 = i + 2 * nw;
         const int u2 = i2 < count ? root(i2) : 0;
         const int4 ru2 = i2 < count ? g.rinfo[u2] : Z;
-        const int v1 = (i + nw < count && lane < ru1.y - ru1.x) ? g.ncol[ru1.x + lane] : -1;
-        int4 rv1 = Z;
-        bool rv1_loaded = false;
+        const int2 s1 = (i + nw < count && lane < ru1.y - ru1.x && ru1.y - ru1.x <= 64) ? g.wl[ru1.x + lane] : Z2;
         [&] {
             const int b = ru.x, din = ru.y - ru.x;
             if (din < 2) return;
             long long W = 0;   // exact wedge count W of root u
             RootChunks rc;
             if (din <= 64) {   // both chunks' segments stay in registers
-                rc.v0 = v0;
-                if (lane < din) {
-                    rc.st0 = rv0.x;
-                    rc.len0 = wedge_len(g, u, rv0);
-                }
+                rc.v0 = lane < din ? g.ncol[b + lane] : -1;   // read only for the credits of repeated keys
+                rc.st0 = s0.x;
+                rc.len0 = s0.y;
                 if (din <= 32) {   // one chunk: its segment table gives W
                     rc.have = 1;
                     rc.total0 = seg_build(S.seg, rc.st0, rc.len0, rc.pre0);
@@ -435,18 +459,16 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
                     rc.have = 2;
                     if (32 + lane < din) {
                         rc.v1 = g.ncol[b + 32 + lane];
-                        const int4 r1 = g.rinfo[rc.v1];
-                        rc.st1 = r1.x;
-                        rc.len1 = wedge_len(g, u, r1);
+                        const int2 sl = g.wl[b + 32 + lane];
+                        rc.st1 = sl.x;
+                        rc.len1 = sl.y;
                     }
                     W = warp_sum(rc.len0 + rc.len1);
                 }
             } else {
-                for (int p = lane; p < din; p += 32) W += wedge_len(g, u, g.rinfo[g.ncol[b + p]]);
+                for (int p = lane; p < din; p += 32) W += wedge_seg(g, u, din, b + p).y;
                 W = warp_sum(W);
             }
-            rv1 = v1 >= 0 ? g.rinfo[v1] : Z;   // next root's in-neighbours, during this walk
-            rv1_loaded = true;
             if (W < 2) return;
             if (W > here_lim) {
                 if (lane == 0) {
@@ -473,13 +495,11 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
                 c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc);
             }
         }();
-        if (!rv1_loaded) rv1 = v1 >= 0 ? g.rinfo[v1] : Z;
         u = un;
         un = u2;
         ru = ru1;
         ru1 = ru2;
-        v0 = v1;
-        rv0 = rv1;
+        s0 = s1;
     }
 }
 
@@ -508,7 +528,7 @@ __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_big_split(Graph g, VA
 // 2 x SLOTS packed ones) lives in dynamic shared memory and is emptied once
 // per CTA.
 template <int THREADS, int SLOTS, int MAXW, bool PACKED>
-__device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count,
+__device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *list, int count, int *next,
                                          int cb) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
@@ -527,7 +547,7 @@ __device__ __forceinline__ void c4_queue(const Graph &g, VAcc *vacc, const int *
     }
     if (threadIdx.x == 0) { flags[0] = 0; flags[1] = 0; }
     __syncthreads();
-    for (int h = blockIdx.x; h < count; h += gridDim.x) {
+    for (int h = cta_next(next); h < count; h = cta_next(next)) {
         const int u = list[h];
         const int4 ru = g.rinfo[u];
         if (PACKED) {
@@ -547,22 +567,22 @@ constexpr size_t cq_smem(int threads, int slots, int maxw) {
 constexpr size_t CM_SMEM = cq_smem(CM_THREADS, CM_SLOTS, CM_MAXW);
 constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXW);
 
-__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists,
-                                                       const int *counters, int cb) {
+// Both 128-thread queues in one launch: the packed one (W <= 6144 with
+// enough count bits), then the split one (W <= 3072).
+__global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists, int *counters,
+                                                       int cb) {
     if (degree_overflow(counters)) return;
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID], cb);
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP],
+                                                  counters + CNT_C4_MIDP_NEXT, cb);
+    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, false>(g, vacc, lists + 2 * (size_t)g.n, counters[CNT_C4_MID],
+                                                   counters + CNT_C4_MID_NEXT, cb);
 }
 
-__global__ void __launch_bounds__(CM_THREADS) k_c4_midp(Graph g, VAcc *vacc, const int *lists,
-                                                        const int *counters, int cb) {
+__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists, int *counters,
+                                                       int cb) {
     if (degree_overflow(counters)) return;
-    c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP], cb);
-}
-
-__global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists,
-                                                       const int *counters, int cb) {
-    if (degree_overflow(counters)) return;
-    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXW, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA], cb);
+    c4_queue<CC_THREADS, CC_SLOTS, CC_MAXW, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA],
+                                                   counters + CNT_C4_CTA_NEXT, cb);
 }
 
 // ------------------------------------------------------ key-tiled tier
@@ -577,11 +597,14 @@ __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, cons
 // are a run of that row: every in-neighbour keeps a cursor (the start of its
 // next run), the end of its wedge prefix and the key at the cursor. A tile
 // first finds every in-neighbour's run (a galloping search from the cursor,
-// one thread per in-neighbour) and marks the chunks of 32 in-neighbours that
-// have one; then it counts the runs' wedges, credits C(c, 2) to every key w
-// and to u from the counts, walks the runs again adding c - 1 per wedge to
-// its middle vertex, and clears. The next tile starts at the smallest key
-// any cursor points at, so key ranges without wedges are skipped.
+// one thread per in-neighbour) and its offset in the concatenation of the
+// tile's runs (a prefix sum across the CTA); every warp then takes an equal
+// slice of that concatenation, so that hub rows do not leave warps waiting.
+// It counts the slice's wedges, credits C(c, 2) to every key w and to u
+// from the counts, walks the slice again adding c - 1 per wedge to its
+// middle vertex, moves the cursors past the runs, and clears. The next tile
+// starts at the smallest key any cursor points at, so key ranges without
+// wedges are skipped.
 // The cursors of all these roots (their in-degrees sum to at most |E|) live
 // in the region of the per-edge triangle counts, which nothing reads after
 // the aggregate stage and which is sized 8 m bytes for them: 16 bytes per
@@ -591,8 +614,7 @@ constexpr int CK_NW = CK_THREADS / 32;
 constexpr int CK_WORDS = 48 * 1024;                 // counter words in shared memory (192 KB)
 constexpr int CK_NARROW_MAXD = 65534;               // in-degree up to which 16-bit counters cannot overflow
 constexpr int CK_INF = 0x7fffffff;
-constexpr int CK_CBITS = (MAX_DEGREE / 32 + 31) / 32;  // words of chunk bits: in-degree <= MAX_DEGREE
-constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + CK_CBITS * 4 + 64;
+constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + 64 * 4;
 static_assert(CK_SMEM <= 227 * 1024, "k_c4_tiled shared memory");
 
 // Root order of the key-tiled tier: the queued roots (list 4, their wedge
@@ -680,26 +702,25 @@ struct TileCounts {
 };
 
 // One root of the key-tiled tier, the whole CTA. st: one int4 per
-// in-neighbour {cursor, end of its wedge prefix, run length in the current
-// tile, key at the cursor}; the run length is 0 outside a tile's passes.
-// cbits: one bit per chunk of 32 in-neighbours with a run in the tile.
+// in-neighbour {cursor, end of its wedge prefix, offset of its run in the
+// tile's concatenation of runs, key at the cursor}. The offsets are scanned
+// per warp over a contiguous range of R in-neighbours (R a multiple of 32,
+// so a chunk never straddles two ranges); woff[r] turns range r's offsets
+// into offsets in the whole tile.
 template <bool WIDE>
 __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u, int4 *st, unsigned *cnt,
-                                              SegTab *segs, long long *pvs, unsigned *cbits, int *s_next) {
+                                              SegTab *segs, long long *pvs, int *ssm) {
     const int lane = lane_id(), wid = threadIdx.x >> 5;
     const int4 ru = g.rinfo[u];
     const int b = ru.x, din = ru.y - ru.x;
-    const int nch = (din + 31) >> 5, nbw = (nch + 31) >> 5;
+    const int nch = (din + 31) >> 5;
     constexpr int TK = CK_WORDS * TileCounts<WIDE>::keys_per_word;
     const TileCounts<WIDE> T{cnt};
     SegTab &seg = segs[wid];
     long long *pv = pvs + wid * 32;
-    // Chunks of 32 in-neighbours: one warp each when there are enough, else
-    // every warp takes every chunk and a share of its windows.
-    const bool shared_chunks = nch < CK_NW;
-    const int c0 = shared_chunks ? 0 : wid, cstep = shared_chunks ? 1 : CK_NW;
-    const int wbase = shared_chunks ? wid * 32 : 0, wstride = shared_chunks ? CK_NW * 32 : 32;
-    auto has_run = [&](int c) { return (cbits[c >> 5] >> (c & 31)) & 1u; };
+    int *woff = ssm, *s_next = ssm + 32, *s_tot = ssm + 33;
+    const int RC = (din + 32 * CK_NW - 1) / (32 * CK_NW), R = RC * 32;   // chunks, in-neighbours per warp range
+    auto offset = [&](int p) { return st[p].z + woff[p / R]; };   // p's run offset in the tile
     // cursors: each in-neighbour v's wedge prefix [row start, position of u in N+(v))
     int mn = CK_INF;
     for (int p = threadIdx.x; p < din; p += CK_THREADS) {
@@ -710,48 +731,90 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
         st[p] = make_int4(rv.x, e, 0, nx);
         mn = min(mn, nx);
     }
+    pv[lane] = 0;
     mn = -warp_max(-mn);
     if (threadIdx.x == 0) *s_next = CK_INF;
-    for (int i = threadIdx.x; i < CK_NW * 32; i += CK_THREADS) pvs[i] = 0;
-    for (int i = threadIdx.x; i < nbw; i += CK_THREADS) cbits[i] = 0;
     __syncthreads();
     if (lane == 0) atomicMin(s_next, mn);
     __syncthreads();
     int lo = *s_next;
     long long su = 0;
+    // The wedges of elements [e0, e1) of the tile's concatenation of runs,
+    // chunk by chunk of 32 in-neighbours: f(act, q, w) per wedge, done(v)
+    // after each chunk.
+    auto visit = [&](long long e0, long long e1, int total, auto f, auto done) {
+        if (e0 >= e1) return;
+        int c = 0, top = nch;   // last chunk whose first run starts at or before e0
+        while (top - c > 1) {
+            const int mid = (c + top) >> 1;
+            if (offset(mid * 32) <= e0) c = mid; else top = mid;
+        }
+        int r = c / RC, left = RC - (c - r * RC);   // warp range of chunk c, chunks left in it
+        for (; c < nch; ++c) {
+            const int p = c * 32 + lane;
+            int v = -1, cur = 0, z = total;
+            if (p < din) {
+                const int4 s4 = st[p];
+                cur = s4.x, z = s4.z + woff[r];
+                v = g.ncol[b + p];
+            }
+            const int cbase = __shfl_sync(FULL, z, 0);
+            if (cbase >= e1) break;
+            int znext = __shfl_down_sync(FULL, z, 1);
+            if (lane == 31) znext = p + 1 < din ? st[p + 1].z + woff[left == 1 ? r + 1 : r] : total;
+            if (--left == 0) {
+                ++r;
+                left = RC;
+            }
+            const int len = p < din ? znext - z : 0;
+            int pre;
+            const int tot = seg_build(seg, cur, len, pre);
+            const int from = (int)max(e0 - cbase, 0ll), to = (int)min(e1 - cbase, (long long)tot);
+            if (from < to)
+                seg_visit<4>(g.ncol, seg, pre, len, to, from, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
+            __syncwarp();
+            done(v);
+            __syncwarp();
+        }
+    };
     while (lo < u) {
         const int hi = min(lo + TK, u);
         const int nk = hi - lo;
-        __syncthreads();
-        if (threadIdx.x == 0) *s_next = CK_INF;
-        // A. the run of every in-neighbour inside [lo, hi), one thread each;
-        // the next key of those without one bounds the next tile
-        int tnext = CK_INF;
-        for (int p = threadIdx.x; p < din; p += CK_THREADS) {
-            const int4 s4 = st[p];
-            if (s4.w < hi) {
-                st[p].z = gallop(g.ncol, s4.x, s4.y, hi) - s4.x;
-                atomicOr(&cbits[p >> 10], 1u << ((p >> 5) & 31));
-            } else {
-                tnext = min(tnext, s4.w);
+        // A. every in-neighbour's run inside [lo, hi) (a galloping search from
+        // its cursor) and the run's offset in the tile's concatenation: each
+        // warp scans its range with a running carry, then one scan of the
+        // warps' totals
+        {
+            int carry = 0;
+            const int r0 = wid * R, r1 = min(r0 + R, din);
+            for (int p0 = r0; p0 < r1; p0 += 32) {
+                const int p = p0 + lane;
+                int len = 0;
+                if (p < r1) {
+                    const int4 s4 = st[p];
+                    if (s4.w < hi) len = gallop(g.ncol, s4.x, s4.y, hi) - s4.x;
+                }
+                const int incl = warp_inclusive_scan(len);
+                if (p < r1) st[p].z = carry + incl - len;
+                carry += __shfl_sync(FULL, incl, 31);
             }
+            if (lane == 0) woff[wid] = carry;
+            __syncthreads();
+            if (wid == 0) {
+                const int x = woff[lane];
+                const int xi = warp_inclusive_scan(x);
+                woff[lane] = xi - x;
+                if (lane == 31) *s_tot = xi;
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        const int total = *s_tot;
+        // every warp takes an equal slice of the tile's wedges
+        const long long e0 = (long long)total * wid / CK_NW, e1 = (long long)total * (wid + 1) / CK_NW;
         // 1. count the tile's wedges
-        for (int c = c0; c < nch; c += cstep) {
-            if (!has_run(c)) continue;
-            const int p = c * 32 + lane;
-            int cur = 0, len = 0, pre;
-            if (p < din) {
-                const int4 s4 = st[p];
-                cur = s4.x, len = s4.z;
-            }
-            const int total = seg_build(seg, cur, len, pre);
-            seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int, int, int w) {
-                if (ok && (unsigned)(w - lo) < (unsigned)nk) T.add(w - lo);   // always, for a simple graph
-            });
-            __syncwarp();
-        }
+        visit(e0, e1, total, [&](bool ok, int, int w) {
+            if (ok && (unsigned)(w - lo) < (unsigned)nk) T.add(w - lo);   // always, for a simple graph
+        }, [](int) {});
         __syncthreads();
         // 2. C(c, 2) to every key with c >= 2 and to u (the counts are only read from here on)
         const int nw4 = (nk + 4 * T.keys_per_word - 1) / (4 * T.keys_per_word);
@@ -772,44 +835,39 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
                 }
             }
         }
-        // 3. middle vertices: c - 1 per wedge, summed per in-neighbour; the
-        // cursors move past the runs
-        for (int c = c0; c < nch; c += cstep) {
-            if (!has_run(c)) continue;
-            const int p = c * 32 + lane;
-            int v = -1, cur = 0, len = 0, end = 0, pre;
-            if (p < din) {
-                v = g.ncol[b + p];
-                const int4 s4 = st[p];
-                cur = s4.x, end = s4.y, len = s4.z;
+        // 3. middle vertices: c - 1 per wedge, summed per in-neighbour
+        visit(e0, e1, total, [&](bool ok, int q, int w) {
+            const bool in = ok && (unsigned)(w - lo) < (unsigned)nk;
+            add_middle(pv, q, in ? T.get(w - lo) : 0);
+        }, [&](int v) {
+            const long long x = pv[lane];
+            if (x) add64(&vacc[v].C4, x);
+            pv[lane] = 0;
+        });
+        if (threadIdx.x == 0) *s_next = CK_INF;
+        __syncthreads();
+        // 4. cursors past the runs; the smallest next key starts the next
+        // tile; clear the tile
+        int tnext = CK_INF;
+        for (int p = wid * R + lane; p < min((wid + 1) * R, din); p += 32) {   // the warp's own range
+            const int4 s4 = st[p];
+            const int z = s4.z + woff[wid];
+            const int len = (p + 1 < din ? st[p + 1].z + woff[p + 1 == (wid + 1) * R ? wid + 1 : wid] : total) - z;
+            int nx = s4.w;
+            if (len > 0) {
+                const int cur = s4.x + len;
+                nx = cur < s4.y ? g.ncol[cur] : CK_INF;
+                st[p].x = cur;
+                st[p].w = nx;
             }
-            const int total = seg_build(seg, cur, len, pre);
-            seg_visit<4>(g.ncol, seg, pre, len, total, wbase, wstride, [&](bool ok, int q, int, int w) {
-                const bool in = ok && (unsigned)(w - lo) < (unsigned)nk;
-                add_middle(shared_chunks ? pvs : pv, q, in ? T.get(w - lo) : 0);
-            });
-            if (shared_chunks) __syncthreads(); else __syncwarp();
-            if (!shared_chunks || wid == 0) {
-                long long *pm = shared_chunks ? pvs : pv;
-                const long long x = pm[lane];
-                if (x) add64(&vacc[v].C4, x);
-                pm[lane] = 0;
-                if (len > 0) {
-                    cur += len;
-                    const int nx = cur < end ? g.ncol[cur] : CK_INF;
-                    st[p] = make_int4(cur, end, 0, nx);
-                    tnext = min(tnext, nx);
-                }
-            }
-            if (shared_chunks) __syncthreads(); else __syncwarp();
+            tnext = min(tnext, nx);
         }
         tnext = -warp_max(-tnext);
         if (lane == 0 && tnext < CK_INF) atomicMin(s_next, tnext);
-        __syncthreads();
-        // 4. clear the tile and the chunk bits
         for (int i = threadIdx.x; i < nw4; i += CK_THREADS) reinterpret_cast<uint4 *>(cnt)[i] = make_uint4(0, 0, 0, 0);
-        for (int i = threadIdx.x; i < nbw; i += CK_THREADS) cbits[i] = 0;
+        __syncthreads();
         lo = *s_next;
+        __syncthreads();
     }
     su = warp_sum(su);
     if (lane == 0 && su) add64(&vacc[u].C4, su);
@@ -824,9 +882,8 @@ __global__ void __launch_bounds__(CK_THREADS) k_c4_tiled(Graph g, VAcc *vacc, co
     unsigned *cnt = reinterpret_cast<unsigned *>(dsm);
     SegTab *segs = reinterpret_cast<SegTab *>(cnt + CK_WORDS);
     long long *pvs = reinterpret_cast<long long *>(segs + CK_NW);
-    unsigned *cbits = reinterpret_cast<unsigned *>(pvs + CK_NW * 32);
-    int *s_next = reinterpret_cast<int *>(cbits + CK_CBITS);
-    int *s_job = s_next + 1;
+    int *ssm = reinterpret_cast<int *>(pvs + CK_NW * 32);   // scan partials, next key, run total
+    int *s_job = ssm + 40;
     if (degree_overflow(counters)) return;
     const int nt = counters[CNT_C4_TEAM];
     if (nt == 0) return;
@@ -846,8 +903,8 @@ __global__ void __launch_bounds__(CK_THREADS) k_c4_tiled(Graph g, VAcc *vacc, co
             continue;
         }
         int4 *st = cursors + offs[j];
-        if (ru.y - ru.x <= CK_NARROW_MAXD) c4_tiled_root<false>(g, vacc, u, st, cnt, segs, pvs, cbits, s_next);
-        else c4_tiled_root<true>(g, vacc, u, st, cnt, segs, pvs, cbits, s_next);
+        if (ru.y - ru.x <= CK_NARROW_MAXD) c4_tiled_root<false>(g, vacc, u, st, cnt, segs, pvs, ssm);
+        else c4_tiled_root<true>(g, vacc, u, st, cnt, segs, pvs, ssm);
     }
 }
 
@@ -860,7 +917,11 @@ static int packed_count_bits(int n) {
 }
 
 void launch_cycle4(Work &w, cudaStream_t st) {
-    Graph g{w.n, w.m, w.rinfo, w.ncol};
+    // the wedge segments take the region of the triangle counts, dead after the aggregate stage
+    int2 *wl = reinterpret_cast<int2 *>(w.tcnt);
+    Graph g{w.n, w.m, w.rinfo, w.ncol, wl};
+    k_c4_wedge_len<<<w.num_sms * 8, 256, 0, st>>>(g, wl, w.counters);
+    after_launch(st, K_C4_WEDGE_LEN);
     const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
     const int cb = packed_count_bits(w.n);
     // a packed word holds counts up to 2^cb - 2; with many vertices (large
@@ -868,25 +929,29 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     // tier counts in split tables instead
     const bool packed = (1ll << cb) - 2 >= maxw;
     const int teamw = w.tune[TUNE_C4_TEAM_MINW];
+    static const int occ_w = resident_ctas((const void *)k_c4_warp, CW_WARPS * 32, 0);
+    static const int occ_ws = resident_ctas((const void *)k_c4_warp_split, CW_WARPS * 32, 0);
+    static const int occ_b = resident_ctas((const void *)k_c4_warp_big, CW_WARPS * 32, 0);
+    static const int occ_bs = resident_ctas((const void *)k_c4_warp_big_split, CW_WARPS * 32, 0);
     if (packed)
-        k_c4_warp<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
+        k_c4_warp<<<w.num_sms * min(w.tune[TUNE_GRID_C4], occ_w), CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
                                                                              cb, teamw);
     else
-        k_c4_warp_split<<<w.num_sms * w.tune[TUNE_GRID_C4], CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters,
+        k_c4_warp_split<<<w.num_sms * min(w.tune[TUNE_GRID_C4], occ_ws), CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters,
                                                                                    maxw, cb, teamw);
     after_launch(st, K_C4_WARP);
     // roots k_c4_warp queued for the 8 KB tables: one resident wave
     if (packed)
-        k_c4_warp_big<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb, teamw);
+        k_c4_warp_big<<<w.num_sms * occ_b, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb, teamw);
     else
-        k_c4_warp_big_split<<<w.num_sms * 6, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb,
+        k_c4_warp_big_split<<<w.num_sms * occ_bs, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb,
                                                                      teamw);
     after_launch(st, K_C4_WARP_BIG);
-    k_c4_midp<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
-    after_launch(st, K_C4_MIDP);
-    k_c4_mid<<<w.num_sms * 4, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    static const int occ_m = resident_ctas((const void *)k_c4_mid, CM_THREADS, CM_SMEM);
+    static const int occ_c = resident_ctas((const void *)k_c4_cta, CC_THREADS, CC_SMEM);
+    k_c4_mid<<<w.num_sms * occ_m, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MID);
-    k_c4_cta<<<w.num_sms, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    k_c4_cta<<<w.num_sms * occ_c, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
     k_c4_tiled_plan<<<1, 1024, 0, st>>>(g, w.lists, w.counters);
     after_launch(st, K_C4_PLAN);
@@ -903,7 +968,6 @@ void configure_cycle4() {
     cudaFuncSetAttribute(k_c4_warp_big, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_c4_warp_big_split, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_c4_mid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
-    cudaFuncSetAttribute(k_c4_midp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CM_SMEM);
     cudaFuncSetAttribute(k_c4_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC_SMEM);
     cudaFuncSetAttribute(k_c4_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CK_SMEM);
 }

@@ -49,8 +49,28 @@ enum TuneIndex {
 // Indices into Work::counters.
 // The triangle and aggregate heavy lists hold two tiers each: CTA-sized
 // roots from the front (CNT_*_HEAVY), the largest from the back (CNT_*_BIG).
+// The *_NEXT entries are the work counters of the CTA tiers: each CTA takes
+// its next root from the queue's counter, so a CTA that starts late (or a
+// root that takes long) leaves no other CTA idle.
 enum { CNT_TRI_HEAVY = 0, CNT_AGG_HEAVY = 1, CNT_C4_CTA = 2, CNT_C4_TEAM = 3, CNT_DMAX = 4, CNT_C4_MID = 5,
-       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8, CNT_C4_WBIG = 9, CNT_C4_TILED_NEXT = 10 };
+       CNT_C4_MIDP = 6, CNT_TRI_BIG = 7, CNT_AGG_BIG = 8, CNT_C4_WBIG = 9, CNT_C4_TILED_NEXT = 10,
+       CNT_TRI_CTA_NEXT = 11, CNT_TRI_BIG_NEXT = 12, CNT_AGG_CTA_NEXT = 13, CNT_AGG_BIG_NEXT = 14,
+       CNT_C4_MID_NEXT = 15, CNT_C4_MIDP_NEXT = 16, CNT_C4_CTA_NEXT = 17, NCOUNTERS = 32 };
+
+// The next item of a work queue, for the whole CTA: thread 0 takes it from
+// the queue's counter, every thread returns the same index.
+__device__ __forceinline__ int cta_next(int *ctr) {
+    __shared__ int s_item;
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
+    __syncthreads();
+    return s_item;
+}
+
+// CTAs of `kernel` (launched with `threads` threads and `smem` bytes of
+// dynamic shared memory) that one SM holds at once: the size of a
+// persistent grid is SMs times this.
+int resident_ctas(const void *kernel, int threads, size_t smem);
 
 // Whether the degree pass found a degree above MAX_DEGREE. NIORCA_EOVERFLOW
 // is then recorded already, and every kernel after the relabelling returns
@@ -81,7 +101,7 @@ void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *st
 enum KernelId {
     K_CLASS_HIST, K_SCAN, K_CLASS_SCATTER, K_RELABEL_WARP, K_RELABEL_CTA, K_BATCH_SETUP,
     K_TRI_WARP, K_TRI_CTA, K_AGG_WARP, K_AGG_CTA, K_C4_WARP, K_C4_CTA, K_C4_PLAN, K_C4_TILED,
-    K_SOLVE, K_VALIDATE, K_C4_MID, K_C4_MIDP, K_TRI_BIG, K_AGG_BIG, K_C4_WARP_BIG, K_COUNT
+    K_SOLVE, K_VALIDATE, K_C4_MID, K_TRI_BIG, K_AGG_BIG, K_C4_WARP_BIG, K_C4_WEDGE_LEN, K_COUNT
 };
 const char *kernel_name(int id);
 

@@ -38,11 +38,20 @@ thread_local Timeline *t_cur = nullptr;
 const char *const kNames[K_COUNT] = {
     "k_class_hist", "k_scan", "k_class_scatter", "k_relabel_rows_warp", "k_relabel_rows_cta", "k_batch_setup",
     "k_tri_warp", "k_tri_cta", "k_agg_warp", "k_agg_cta", "k_c4_warp", "k_c4_cta", "k_c4_tiled_plan",
-    "k_c4_tiled", "k_solve", "k_validate", "k_c4_mid", "k_c4_midp", "k_tri_big", "k_agg_big",
-    "k_c4_warp_big"};
+    "k_c4_tiled", "k_solve", "k_validate", "k_c4_mid", "k_tri_big", "k_agg_big",
+    "k_c4_warp_big", "k_c4_wedge_len"};
 }  // namespace
 
 const char *kernel_name(int id) { return (id >= 0 && id < K_COUNT) ? kNames[id] : "?"; }
+
+int resident_ctas(const void *kernel, int threads, size_t smem) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        n = 1;
+    }
+    return n > 0 ? n : 1;
+}
 
 void after_launch(cudaStream_t st, int id) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -184,7 +193,7 @@ Layout plan(long long n, long long m, int num_sms, bool batch) {
     const size_t sp1 = scan_partials(NCLASS * nt), sp2 = scan_partials(n);
     L.scan_part = take(4 * (sp1 > sp2 ? sp1 : sp2));
     L.lists = take(4 * 6 * n);
-    L.counters = take(4 * 16);
+    L.counters = take(4 * NCOUNTERS);
     L.vrange = batch ? take(8 * n) : 0;
     L.total = o;
     return L;
@@ -235,7 +244,7 @@ niorca_status run(const int *rowptr, const int *colidx, int n, int m, long long 
     w.num_sms = ds->num_sms;
     for (int i = 0; i < TUNE_COUNT; ++i) w.tune[i] = ds->tune[i];
     w.induced = induced;
-    cudaMemsetAsync(w.counters, 0, 4 * 16, st);
+    cudaMemsetAsync(w.counters, 0, 4 * NCOUNTERS, st);
     timeline_begin(st);
     if (batch) {
         int2 *vrange = reinterpret_cast<int2 *>(b + L.vrange);

@@ -91,7 +91,7 @@ size_t carve(unsigned char *base, long long n, long long m, Work *w) {
     const size_t sp1 = scan_partials(NCLASS * nt), sp2 = scan_partials(n);
     w->scan_part = reinterpret_cast<int *>(take(4 * (sp1 > sp2 ? sp1 : sp2)));
     w->lists = reinterpret_cast<int *>(take(4 * 6 * n));
-    w->counters = reinterpret_cast<int *>(take(4 * 16));
+    w->counters = reinterpret_cast<int *>(take(4 * NCOUNTERS));
     w->ntiles = (int)nt;
     return o;
 }
@@ -118,7 +118,7 @@ extern "C" niorca_status niorca_count_noalloc(const int32_t *rowptr, const int32
     w.status = status ? reinterpret_cast<int *>(status) : d->status;
     w.num_sms = d->num_sms;
     if (cudaMemsetAsync(w.status, 0, sizeof(int), st) != cudaSuccess) return NIORCA_ECUDA;
-    if (cudaMemsetAsync(w.counters, 0, 4 * 16, st) != cudaSuccess) return NIORCA_ECUDA;
+    if (cudaMemsetAsync(w.counters, 0, 4 * NCOUNTERS, st) != cudaSuccess) return NIORCA_ECUDA;
     launch_relabel(rowptr, colidx, w, st);
     launch_stage1(w, st);
     launch_stage2(w, st);

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(int *part, int nblocks) {
     if (threadIdx.x == 0) part[nblocks] = carry;
 }
 
+// With part == nullptr a single block scans the whole array (len <= SCAN_TILE).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int *in, int *out, long long len, const int *part,
                                                            int write_total) {
     __shared__ int tile[SCAN_TILE];
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int *in, int *
         local[k] = tile[threadIdx.x * SCAN_PER_THREAD + k];
         s += local[k];
     }
-    int ex = block_exclusive_scan(s, wsum, &tot) + part[blockIdx.x];
+    int ex = block_exclusive_scan(s, wsum, &tot) + (part ? part[blockIdx.x] : 0);
 #pragma unroll
     for (int k = 0; k < SCAN_PER_THREAD; ++k) {
         tile[threadIdx.x * SCAN_PER_THREAD + k] = ex;
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int *in, int *
         long long g = base + i;
         if (g < len) out[g] = tile[i];
     }
-    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[len] = part[gridDim.x];
+    if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[len] = part ? part[gridDim.x] : tot;
 }
 
 void launch_exclusive_scan(const int *in, int *out, long long len, bool write_total, int *part,
@@ -105,6 +106,11 @@ void launch_exclusive_scan(const int *in, int *out, long long len, bool write_to
     const int nb = (int)((len + SCAN_TILE - 1) / SCAN_TILE);
     if (nb == 0) {
         if (write_total) cudaMemsetAsync(out, 0, sizeof(int), st);
+        return;
+    }
+    if (nb == 1) {   // one tile: one launch
+        k_scan_down<<<1, SCAN_THREADS, 0, st>>>(in, out, len, nullptr, write_total ? 1 : 0);
+        after_launch(st, K_SCAN);
         return;
     }
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, len, part);
@@ -412,6 +418,8 @@ static void relabel_common(const int *rowptr, const int *colidx, const int2 *vra
     after_launch(st, K_CLASS_SCATTER);
     launch_exclusive_scan(w.split, w.nrow, w.n, true, w.scan_part, st);
     const int lrc = w.tune[TUNE_LONG_ROW_CLASS];
+    // more CTAs than an SM holds: with rows of uneven length, the later
+    // waves act as load balancing
     k_relabel_rows_warp<<<w.num_sms * w.tune[TUNE_GRID_RELABEL], 256, 0, st>>>(
         rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow, w.coff, nt, w.ncol, w.rinfo, w.vacc, w.tcnt, w.status,
         lrc);

@@ -136,14 +136,14 @@ __global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, 
 // Roots with out-degree above the warp tier get a CTA each, in two sizes:
 // k_tri_cta (256 threads, dp <= TS_MAXD) needs about 18 KB of shared memory,
 // so several CTAs share an SM; k_tri_big (1024 threads) takes the rest with
-// the bit matrix R up to TB_BITMAT_MAXD (hash of N+(u) capped at 2048 slots),
+// the bit matrix R up to TB_BITMAT_MAXD (hash of N+(u) capped at 4096 slots),
 // a 16384-slot hash up to TB_HASH_MAXD, and binary searches beyond.
 // k_tri_warp queues the first kind from the front of the heavy list and the
 // second from its back.
 constexpr int TS_THREADS = 256;
 constexpr int TB_THREADS = 1024;
 constexpr int TB_BITMAT_MAXD = 1152;
-constexpr int TB_BITMAT_HSLOTS = 2048;
+constexpr int TB_BITMAT_HSLOTS = 4096;
 constexpr int TB_HASH_MAXD = 8192;
 
 // Dynamic shared memory of one CTA: hash keys + values (hslots), cnt + kc
@@ -154,7 +154,7 @@ constexpr size_t tc_smem(int threads, int hslots, int nloc, int rows) {
     return (size_t)2 * hslots * 4 + (size_t)2 * nloc * 4 + (size_t)(threads / 32) * (sizeof(SegTab) + 128) + 16 +
            (size_t)rows * tc_rowstride(rows) * 4;
 }
-constexpr size_t TS_SMEM = tc_smem(TS_THREADS, 2 * TS_MAXD, TS_MAXD, TS_MAXD);
+constexpr size_t TS_SMEM = tc_smem(TS_THREADS, 4 * TS_MAXD, TS_MAXD, TS_MAXD);
 constexpr size_t TB_SMEM_BITS = tc_smem(TB_THREADS, TB_BITMAT_HSLOTS, TB_BITMAT_MAXD, TB_BITMAT_MAXD);
 constexpr size_t TB_SMEM_HASH = tc_smem(TB_THREADS, 2 * TB_HASH_MAXD, TB_HASH_MAXD, 0);
 constexpr size_t TB_SMEM = TB_SMEM_BITS > TB_SMEM_HASH ? TB_SMEM_BITS : TB_SMEM_HASH;
@@ -172,21 +172,22 @@ __device__ __forceinline__ int out_index(const int *hk, const int *hv, unsigned 
 // bits_maxd and the hash of N+(u) up to hash_maxd (run-time limits no larger
 // than the compiled ones, bits_maxd <= hash_maxd), else it probes N+(u) by
 // binary search and enumerates the K4 of each triangle.
-template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK>
+template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK, int HMUL>
 __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, const int *list, int count,
-                                        int bits_maxd, int hash_maxd) {
+                                        int *next, int bits_maxd, int hash_maxd) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int TC_THREADS = THREADS;
     constexpr int NW = THREADS / 32;
     const int lane = lane_id(), wid = threadIdx.x >> 5;
-    for (int h = blockIdx.x; h < count; h += gridDim.x) {
+    for (int h = cta_next(next); h < count; h = cta_next(next)) {
         const int u = BACK ? list[g.n - 1 - h] : list[h];
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
         const bool use_hash = dp <= HASH_MAXD && dp <= hash_maxd;
         const bool use_bits = use_hash && dp <= BITMAT_MAXD && dp <= bits_maxd;
-        unsigned H = use_hash ? next_pow2(2 * dp) : 0;
-        if (use_bits && H > (unsigned)BITMAT_HSLOTS) H = BITMAT_HSLOTS;
+        unsigned H = use_hash ? next_pow2(HMUL * dp) : 0;   // hash load at most 1 / HMUL, within the carve:
+        const unsigned hcap = use_bits ? BITMAT_HSLOTS : 2 * HASH_MAXD;   // its mode's slots
+        if (H > hcap) H = hcap;
         const unsigned mask = H ? H - 1 : 0;
         const int W = (dp + 31) >> 5;  // bit-matrix words per row
         const int WP = W | 1;          // row stride of R
@@ -358,17 +359,18 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
 }
 
 __global__ void __launch_bounds__(TS_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters, int bits_maxd, int hash_maxd) {
+                                                        int *counters, int bits_maxd, int hash_maxd) {
     if (degree_overflow(counters)) return;
-    tri_cta<TS_THREADS, TS_MAXD, 2 * TS_MAXD, TS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_TRI_HEAVY],
-                                                            bits_maxd, hash_maxd);
+    tri_cta<TS_THREADS, TS_MAXD, 4 * TS_MAXD, TS_MAXD, false, 4>(g, tcnt, vacc, heavy, counters[CNT_TRI_HEAVY],
+                                                            counters + CNT_TRI_CTA_NEXT, bits_maxd, hash_maxd);
 }
 
 __global__ void __launch_bounds__(TB_THREADS) k_tri_big(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters, int bits_maxd, int hash_maxd) {
+                                                        int *counters, int bits_maxd, int hash_maxd) {
     if (degree_overflow(counters)) return;
-    tri_cta<TB_THREADS, TB_BITMAT_MAXD, TB_BITMAT_HSLOTS, TB_HASH_MAXD, true>(g, tcnt, vacc, heavy,
-                                                                            counters[CNT_TRI_BIG], bits_maxd,
+    tri_cta<TB_THREADS, TB_BITMAT_MAXD, TB_BITMAT_HSLOTS, TB_HASH_MAXD, true, 4>(g, tcnt, vacc, heavy,
+                                                                            counters[CNT_TRI_BIG],
+                                                                            counters + CNT_TRI_BIG_NEXT, bits_maxd,
                                                                             hash_maxd);
 }
 
@@ -376,13 +378,16 @@ __global__ void __launch_bounds__(TB_THREADS) k_tri_big(Graph g, int *tcnt, VAcc
 void launch_stage1(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     const int maxd = w.tune[TUNE_WARP_MAXD] < TW_MAXD ? w.tune[TUNE_WARP_MAXD] : TW_MAXD;
-    k_tri_warp<<<w.num_sms * w.tune[TUNE_GRID_TRI], TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters,
-                                                                          maxd);
+    static const int occ_w = resident_ctas((const void *)k_tri_warp, TW_WARPS * 32, 0);
+    static const int occ_c = resident_ctas((const void *)k_tri_cta, TS_THREADS, TS_SMEM);
+    static const int occ_b = resident_ctas((const void *)k_tri_big, TB_THREADS, TB_SMEM);
+    k_tri_warp<<<w.num_sms * min(w.tune[TUNE_GRID_TRI], occ_w), TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists,
+                                                                                       w.counters, maxd);
     after_launch(st, K_TRI_WARP);
     const int bits = w.tune[TUNE_TRI_BITS_MAXD], hash = w.tune[TUNE_TRI_HASH_MAXD];
-    k_tri_cta<<<w.num_sms * 6, TS_THREADS, TS_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
+    k_tri_cta<<<w.num_sms * occ_c, TS_THREADS, TS_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
     after_launch(st, K_TRI_CTA);
-    k_tri_big<<<w.num_sms, TB_THREADS, TB_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
+    k_tri_big<<<w.num_sms * occ_b, TB_THREADS, TB_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
     after_launch(st, K_TRI_BIG);
 }
 

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *
 constexpr int AS_THREADS = 256;
 constexpr int AB_THREADS = 1024;
 constexpr int AB_BITMAT_MAXD = 1152;
-constexpr int AB_BITMAT_HSLOTS = 2048;
+constexpr int AB_BITMAT_HSLOTS = 4096;
 constexpr int AB_HASH_MAXD = 8192;
 constexpr int ac_rowstride(int rows) { return ((rows + 31) / 32) | 1; }
 // dc (nloc x 8 B, hash-only mode), hash (2 x hslots ints), t(u, .) cache
@@ -135,20 +135,20 @@ constexpr size_t ac_smem(int threads, int hslots, int nloc, int rows) {
     return (size_t)nloc * 8 + (size_t)2 * hslots * 4 + (size_t)rows * 4 + (size_t)(threads / 32) * (sizeof(SegTab) + 128) +
            16 + (size_t)rows * ac_rowstride(rows) * 4;
 }
-constexpr size_t AS_SMEM = ac_smem(AS_THREADS, 2 * AS_MAXD, 0, AS_MAXD);
+constexpr size_t AS_SMEM = ac_smem(AS_THREADS, 4 * AS_MAXD, 0, AS_MAXD);
 constexpr size_t AB_SMEM_BITS = ac_smem(AB_THREADS, AB_BITMAT_HSLOTS, 0, AB_BITMAT_MAXD);
 constexpr size_t AB_SMEM_HASH = ac_smem(AB_THREADS, 2 * AB_HASH_MAXD, AB_HASH_MAXD, 0);
 constexpr size_t AB_SMEM = AB_SMEM_BITS > AB_SMEM_HASH ? AB_SMEM_BITS : AB_SMEM_HASH;
 static_assert(AB_SMEM <= 227 * 1024, "k_agg_big shared memory");
 
-template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK>
+template <int THREADS, int BITMAT_MAXD, int BITMAT_HSLOTS, int HASH_MAXD, bool BACK, int HMUL>
 __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *vacc, const int *heavy, int nh,
-                                        int bits_maxd, int hash_maxd) {
+                                        int *next, int bits_maxd, int hash_maxd) {
     extern __shared__ __align__(16) unsigned char dsm[];
     constexpr int NW = THREADS / 32;
     __shared__ int any_tri;
     const int lane = lane_id(), wid = threadIdx.x >> 5;
-    for (int h = blockIdx.x; h < nh; h += gridDim.x) {
+    for (int h = cta_next(next); h < nh; h = cta_next(next)) {
         const int u = BACK ? heavy[g.n - 1 - h] : heavy[h];
         const int4 ru = g.rinfo[u];
         const int s = ru.y, e = ru.z, dp = e - s;
@@ -159,8 +159,9 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
         if (!any_tri) continue;
         const bool use_hash = dp <= HASH_MAXD && dp <= hash_maxd;
         const bool use_bits = use_hash && dp <= BITMAT_MAXD && dp <= bits_maxd;
-        unsigned H = use_hash ? next_pow2(2 * dp) : 0;
-        if (use_bits && H > (unsigned)BITMAT_HSLOTS) H = BITMAT_HSLOTS;
+        unsigned H = use_hash ? next_pow2(HMUL * dp) : 0;   // hash load at most 1 / HMUL, within the carve:
+        const unsigned hcap = use_bits ? BITMAT_HSLOTS : 2 * HASH_MAXD;   // its mode's slots
+        if (H > hcap) H = hcap;
         const unsigned mask = H ? H - 1 : 0;
         const int W = (dp + 31) >> 5, WP = W | 1;   // words per row of R, row stride
         const int nloc = (use_hash && !use_bits) ? dp : 0;
@@ -272,17 +273,18 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
 }
 
 __global__ void __launch_bounds__(AS_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters, int bits_maxd, int hash_maxd) {
+                                                        int *counters, int bits_maxd, int hash_maxd) {
     if (degree_overflow(counters)) return;
-    agg_cta<AS_THREADS, AS_MAXD, 2 * AS_MAXD, AS_MAXD, false>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY],
-                                                            bits_maxd, hash_maxd);
+    agg_cta<AS_THREADS, AS_MAXD, 4 * AS_MAXD, AS_MAXD, false, 4>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY],
+                                                            counters + CNT_AGG_CTA_NEXT, bits_maxd, hash_maxd);
 }
 
 __global__ void __launch_bounds__(AB_THREADS) k_agg_big(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
-                                                        const int *counters, int bits_maxd, int hash_maxd) {
+                                                        int *counters, int bits_maxd, int hash_maxd) {
     if (degree_overflow(counters)) return;
-    agg_cta<AB_THREADS, AB_BITMAT_MAXD, AB_BITMAT_HSLOTS, AB_HASH_MAXD, true>(g, tcnt, vacc, heavy,
-                                                                            counters[CNT_AGG_BIG], bits_maxd,
+    agg_cta<AB_THREADS, AB_BITMAT_MAXD, AB_BITMAT_HSLOTS, AB_HASH_MAXD, true, 4>(g, tcnt, vacc, heavy,
+                                                                            counters[CNT_AGG_BIG],
+                                                                            counters + CNT_AGG_BIG_NEXT, bits_maxd,
                                                                             hash_maxd);
 }
 
@@ -290,13 +292,16 @@ void launch_stage2(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
     int *heavy = w.lists + (size_t)w.n;
     const int maxd = w.tune[TUNE_WARP_MAXD] < AW_MAXD ? w.tune[TUNE_WARP_MAXD] : AW_MAXD;
-    k_agg_warp<<<w.num_sms * w.tune[TUNE_GRID_AGG], AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy, w.counters,
-                                                                          maxd);
+    static const int occ_w = resident_ctas((const void *)k_agg_warp, AW_WARPS * 32, 0);
+    static const int occ_c = resident_ctas((const void *)k_agg_cta, AS_THREADS, AS_SMEM);
+    static const int occ_b = resident_ctas((const void *)k_agg_big, AB_THREADS, AB_SMEM);
+    k_agg_warp<<<w.num_sms * min(w.tune[TUNE_GRID_AGG], occ_w), AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy,
+                                                                                       w.counters, maxd);
     after_launch(st, K_AGG_WARP);
     const int bits = w.tune[TUNE_TRI_BITS_MAXD], hash = w.tune[TUNE_TRI_HASH_MAXD];
-    k_agg_cta<<<w.num_sms * 6, AS_THREADS, AS_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
+    k_agg_cta<<<w.num_sms * occ_c, AS_THREADS, AS_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
     after_launch(st, K_AGG_CTA);
-    k_agg_big<<<w.num_sms, AB_THREADS, AB_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
+    k_agg_big<<<w.num_sms * occ_b, AB_THREADS, AB_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
     after_launch(st, K_AGG_BIG);
 }
 

@@ -51,12 +51,12 @@ def test_four_cycle_tiers_partition_the_wedges(pad):
     rp = np.concatenate([rp, np.full(pad, rp[-1], rp.dtype)])
     ab = bench.algorithmic_bytes(rp, ci)
     tiers = {k: v for k, v in ab["per_kernel"].items() if k.startswith("k_c4")}
-    assert set(tiers) == {"k_c4_warp", "k_c4_warp_big", "k_c4_midp", "k_c4_mid", "k_c4_cta", "k_c4_tiled"}
+    assert set(tiers) == {"k_c4_warp", "k_c4_warp_big", "k_c4_mid", "k_c4_cta", "k_c4_tiled"}
     assert 0 < sum(tiers.values()) <= ab["B_c4"]
     assert ab["B_c4"] - sum(tiers.values()) < 0.001 * ab["B_c4"]
     assert tiers["k_c4_warp"] > 0 and tiers["k_c4_warp_big"] > 0
     if pad:   # split tables: the warp tiers stop at W = 576 and 768
-        assert tiers["k_c4_mid"] > 0 or tiers["k_c4_midp"] > 0
+        assert tiers["k_c4_mid"] > 0
 
 
 def test_deg_class_matches_library_rule():

@@ -81,7 +81,7 @@ def test_four_cycle_warp_tiers_both_table_kinds(ni, pad):
     exp[:10000] = oracle.count(rp, ci)
     rpf = np.concatenate([rp, np.full(pad, rp[-1], rp.dtype)])
     tiers = bench.algorithmic_bytes(rpf, ci)["per_kernel"]
-    assert tiers["k_c4_warp"] > 0 and tiers["k_c4_warp_big"] > 0 and tiers["k_c4_midp"] > 0
+    assert tiers["k_c4_warp"] > 0 and tiers["k_c4_warp_big"] > 0 and tiers["k_c4_mid"] > 0
     assert_same(gpu_count(ni, rpf, ci), exp, f"ER core + {pad} isolated vertices")
 
 
