@@ -36,9 +36,10 @@ WORKLOAD = "Erdos-Renyi G(n=1e6, mean degree 32), seed 1+rank; CSR int32; int64 
 REF_SAMPLE_N = 1 << 17
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dominant kernel on the default workload, from an ncu capture
-# (profiles/er1e6_warp_tier_kernels_full.md), with a hash of the sources the
-# kernel was built from: the bench reports the figure only while they match.
+# the dominant kernel on the default workload, from one ncu capture of that
+# kernel (its summary is kept with the other profiles), with a hash of the
+# sources the kernel was built from: the bench reports the figure only while
+# they match, so a changed kernel reports null until it is captured again.
 NCU_TRAFFIC = {
     "k_c4_warp": {"bytes": 1062572000 + 14857216, "sources": ("csrc/cycle4.cu", "csrc/common.cuh"),
                   "sha256_16": "1d2732cbc115eb0e"},

@@ -752,10 +752,10 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
         int r = c / RC, left = RC - (c - r * RC);   // warp range of chunk c, chunks left in it
         for (; c < nch; ++c) {
             const int p = c * 32 + lane;
-            int v = -1, cur = 0, z = total;
+            int v = -1, cur = 0, end = 0, z = total;
             if (p < din) {
                 const int4 s4 = st[p];
-                cur = s4.x, z = s4.z + woff[r];
+                cur = s4.x, end = s4.y, z = s4.z + woff[r];
                 v = g.ncol[b + p];
             }
             const int cbase = __shfl_sync(FULL, z, 0);
@@ -766,7 +766,8 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
                 ++r;
                 left = RC;
             }
-            const int len = p < din ? znext - z : 0;
+            // the run, never past the in-neighbour's wedge prefix
+            const int len = p < din ? min(max(znext - z, 0), end - cur) : 0;
             int pre;
             const int tot = seg_build(seg, cur, len, pre);
             const int from = (int)max(e0 - cbase, 0ll), to = (int)min(e1 - cbase, (long long)tot);
@@ -800,10 +801,10 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
             }
             if (lane == 0) woff[wid] = carry;
             __syncthreads();
-            if (wid == 0) {
-                const int x = woff[lane];
+            if (wid == 0) {   // the warps' totals, CK_NW of them
+                const int x = lane < CK_NW ? woff[lane] : 0;
                 const int xi = warp_inclusive_scan(x);
-                woff[lane] = xi - x;
+                if (lane < CK_NW) woff[lane] = xi - x;
                 if (lane == 31) *s_tot = xi;
             }
             __syncthreads();
@@ -855,7 +856,7 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
             const int len = (p + 1 < din ? st[p + 1].z + woff[p + 1 == (wid + 1) * R ? wid + 1 : wid] : total) - z;
             int nx = s4.w;
             if (len > 0) {
-                const int cur = s4.x + len;
+                const int cur = s4.x + min(len, s4.y - s4.x);   // never past the wedge prefix
                 nx = cur < s4.y ? g.ncol[cur] : CK_INF;
                 st[p].x = cur;
                 st[p].w = nx;
@@ -955,7 +956,8 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     after_launch(st, K_C4_CTA);
     k_c4_tiled_plan<<<1, 1024, 0, st>>>(g, w.lists, w.counters);
     after_launch(st, K_C4_PLAN);
-    k_c4_tiled<<<w.num_sms, CK_THREADS, CK_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
+    static const int occ_t = resident_ctas((const void *)k_c4_tiled, CK_THREADS, CK_SMEM);
+    k_c4_tiled<<<w.num_sms * occ_t, CK_THREADS, CK_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
                                                       reinterpret_cast<int4 *>(w.tcnt), (long long)w.m / 2,
                                                       w.status);
     after_launch(st, K_C4_TILED);

@@ -30,7 +30,7 @@ constexpr int TW_MAXD = 64;   // out-degree handled by one warp
 constexpr int TS_MAXD = 256;  // out-degree handled by a 256-thread CTA (k_tri_cta)
 constexpr int TW_WARPS = 8;
 
-struct TriWarpSmem {
+struct __align__(16) TriWarpSmem {
     int hk[4 * TW_MAXD];   // N+(u) hash at load <= 1/4 (most probes are misses)
     int hv[4 * TW_MAXD];
     int cnt[TW_MAXD];
@@ -39,7 +39,7 @@ struct TriWarpSmem {
     SegTab seg;
 };
 
-__global__ void __launch_bounds__(TW_WARPS * 32) k_tri_warp(Graph g, int *tcnt, VAcc *vacc, int *heavy,
+__global__ void __launch_bounds__(TW_WARPS * 32, 8) k_tri_warp(Graph g, int *tcnt, VAcc *vacc, int *heavy,
                                                             int *counters, int maxd) {
     __shared__ TriWarpSmem sm_all[TW_WARPS];
     TriWarpSmem &S = sm_all[threadIdx.x >> 5];

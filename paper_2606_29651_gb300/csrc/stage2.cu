@@ -20,7 +20,7 @@ constexpr int AW_MAXD = 64;
 constexpr int AW_WARPS = 8;
 constexpr int AS_MAXD = 256;   // out-degree handled by a 256-thread CTA (k_agg_cta)
 
-struct AggWarpSmem {
+struct __align__(16) AggWarpSmem {
     int hk[4 * AW_MAXD];   // N+(u) hash at load <= 1/4 (most probes are misses)
     int hv[4 * AW_MAXD];
     long long dc[AW_MAXD];
@@ -57,7 +57,7 @@ __device__ __forceinline__ bool edge_aggregates(const Graph &g, const int *tcnt,
     return a1 != 0;
 }
 
-__global__ void __launch_bounds__(AW_WARPS * 32) k_agg_warp(Graph g, const int *tcnt, VAcc *vacc, int *heavy,
+__global__ void __launch_bounds__(AW_WARPS * 32, 8) k_agg_warp(Graph g, const int *tcnt, VAcc *vacc, int *heavy,
                                                             int *counters, int maxd) {
     __shared__ AggWarpSmem sm_all[AW_WARPS];
     AggWarpSmem &S = sm_all[threadIdx.x >> 5];
@@ -167,7 +167,7 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
         const int nloc = (use_hash && !use_bits) ? dp : 0;
         const int nrow = use_bits ? dp : 0;
         long long *dc = reinterpret_cast<long long *>(dsm);   // hash-only mode
-        int *hk = reinterpret_cast<int *>(dc + nloc);
+        int *hk = reinterpret_cast<int *>(dc + ((nloc + 1) & ~1));   // 16-byte aligned buckets
         int *hv = hk + H;
         int *T = hv + H;                                       // t(u, N+(u)[i]), bit-matrix mode
         SegTab *segs = reinterpret_cast<SegTab *>(T + nrow);
