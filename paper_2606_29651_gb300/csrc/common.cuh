@@ -126,21 +126,24 @@ __device__ __forceinline__ int hset_find(const int *keys, const int *vals, unsig
     return -1;
 }
 
-// Warp-aggregated atomic add of `v` to *p among the lanes (of those calling
-// with `active`) that share the same address: one atomic per address.
-__device__ __forceinline__ void warp_add_int(bool active, int *p, int key, int v) {
-    const unsigned peers = __match_any_sync(FULL, active ? key : -1 - lane_id());
-    const unsigned total = __reduce_add_sync(peers, active ? (unsigned)v : 0u);
-    if (active && (peers & lanemask_lt()) == 0) atomicAdd(p, (int)total);
-}
-
-// Same for a 64-bit counter; v >= 0 and below 2^26, so the sum over a warp
-// fits 32 bits (every t is at most the 2^20 degree bound).
-__device__ __forceinline__ void warp_add_ll(bool active, long long *p, int key, int v) {
-    const unsigned peers = __match_any_sync(FULL, active ? key : -1 - lane_id());
-    const unsigned total = __reduce_add_sync(peers, active ? (unsigned)v : 0u);
-    if (active && (peers & lanemask_lt()) == 0)
-        atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(total));
+// Adds each run's sum of v to *p, once per run, where a run is a maximal
+// group of adjacent lanes with the same key (the segments of a
+// concatenation are such runs): the run's last lane adds the difference of
+// the warp's inclusive scan at itself and before the run's first lane.
+// Every lane calls it, each with its own key's p; v >= 0 and the sum over
+// 32 lanes fits 32 bits. Grouping lanes with a warp match instead measured
+// far slower on this GPU, and one atomic per lane serialises on a single
+// 64-bit word when a whole window comes from one long row.
+__device__ __forceinline__ void run_add(long long *p, int key, unsigned v) {
+    const int lane = lane_id();
+    const int kp = __shfl_up_sync(FULL, key, 1);
+    const int kn = __shfl_down_sync(FULL, key, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || kp != key);
+    const int rs = 31 - __clz(heads & ((2u << lane) - 1u));   // first lane of this lane's run
+    const unsigned incl = warp_inclusive_scan(v);
+    const unsigned before = __shfl_sync(FULL, incl - v, rs);
+    if ((lane == 31 || kn != key) && incl != before)
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(incl - before));
 }
 
 // Per-warp table of the segments of one chunk (one segment per lane, e.g. the

@@ -44,14 +44,11 @@ constexpr unsigned EMPTY = 0xffffffffu;
 
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
-// Adds c - 1 to pv[q] for the lanes with c > 1: one warp-aggregated atomic
-// per in-neighbour when many lanes take part (long rows of hub roots), plain
-// shared atomics when few do.
+// Adds c - 1 to pv[q] (shared) for the lanes with c > 1; lanes of one
+// in-neighbour q are consecutive in a window, so one add per run.
 __device__ __forceinline__ void add_middle(long long *pv, int q, int c) {
-    const unsigned m = __ballot_sync(FULL, c > 1);
-    if (!m) return;
-    if (__popc(m) > 8) warp_add_ll(c > 1, &pv[q], q, c - 1);
-    else if (c > 1) atomicAdd(reinterpret_cast<unsigned long long *>(&pv[q]), (unsigned long long)(c - 1));
+    if (!__any_sync(FULL, c > 1)) return;
+    run_add(&pv[q], q, c > 1 ? (unsigned)(c - 1) : 0u);
 }
 
 // Wedges u - v - w through the in-neighbour v of root u: the entries of row

@@ -86,13 +86,9 @@ __global__ void __launch_bounds__(TW_WARPS * 32, 8) k_tri_warp(Graph g, int *tcn
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
-                // lanes of one segment share t(u, v) and words of R: one atomic each
-                warp_add_int(hit, &S.cnt[jj], jj, 1);
-                const int word = jj * 2 + (i >> 5);
-                const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
-                const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
                 if (hit) {
-                    if ((peers & lanemask_lt()) == 0) atomicOr(&S.R[0][0] + word, bits);
+                    atomicAdd(&S.cnt[jj], 1);
+                    atomicOr(&S.R[0][0] + jj * 2 + (i >> 5), 1u << (i & 31));
                     atomicAdd(&S.cnt[i], 1);
                     atomicAdd(&tcnt[pos], 1);
                     found = 1;
@@ -236,15 +232,14 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
                 if (use_bits) {
                     // the upper half of R only; t(u, v) and t(u, w) follow
                     // from R's rows once it is symmetric
-                    const int word = jj * WP + (i >> 5);
-                    const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
-                    const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
-                    if (hit && (peers & lanemask_lt()) == 0) atomicOr(&R[word], bits);
-                    if (hit) atomicAdd(&tcnt[pos], 1);
+                    if (hit) {
+                        atomicOr(&R[jj * WP + (i >> 5)], 1u << (i & 31));
+                        atomicAdd(&tcnt[pos], 1);
+                    }
                     return;
                 }
-                warp_add_int(hit, use_hash ? &cnt[jj] : &tcnt[s + jj], jj, 1);
                 if (!hit) return;
+                atomicAdd(use_hash ? &cnt[jj] : &tcnt[s + jj], 1);
                 atomicAdd(use_hash ? &cnt[i] : &tcnt[s + i], 1);
                 atomicAdd(&tcnt[pos], 1);
                 {

@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(AW_WARPS * 32, 8) k_agg_warp(Graph g, const in
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
                 const int jj = jb + q;
-                warp_add_ll(hit, &S.dc[jj], jj, hit ? tcnt[s + i] - 1 : 0);   // t(u, w) - 1 -> v
                 if (!hit) return;
+                add64(&S.dc[jj], tcnt[s + i] - 1);                           // t(u, w) - 1 -> v
                 du12 += tcnt[pos] - 1;                                       // t(v, w) - 1 -> u
                 atomicAdd((unsigned long long *)&S.dc[i], (unsigned long long)(tcnt[s + jj] - 1));  // t(u, v) - 1 -> w
             });
@@ -211,15 +211,11 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
                 const int jj = jb + q;
                 if (hit) du12 += tcnt[pos] - 1;   // t(v, w) - 1 -> u
                 if (use_bits) {
-                    const int word = jj * WP + (i >> 5);
-                    const unsigned peers = __match_any_sync(FULL, hit ? word : -1 - lane);
-                    const unsigned bits = __reduce_or_sync(peers, hit ? 1u << (i & 31) : 0u);
-                    if (hit && (peers & lanemask_lt()) == 0) atomicOr(&R[word], bits);
+                    if (hit) atomicOr(&R[jj * WP + (i >> 5)], 1u << (i & 31));
                     return;
                 }
-                const int tv = hit ? tcnt[s + i] - 1 : 0;
-                warp_add_ll(hit, use_hash ? &dc[jj] : &vacc[g.ncol[s + jj]].D12, jj, tv);   // t(u, w) - 1 -> v
                 if (!hit) return;
+                add64(use_hash ? &dc[jj] : &vacc[g.ncol[s + jj]].D12, tcnt[s + i] - 1);   // t(u, w) - 1 -> v
                 const long long tw = tcnt[s + jj] - 1;                                      // t(u, v) - 1 -> w
                 if (use_hash) atomicAdd((unsigned long long *)&dc[i], (unsigned long long)tw);
                 else add64(&vacc[w].D12, tw);
