@@ -45,10 +45,19 @@ constexpr unsigned EMPTY = 0xffffffffu;
 __device__ __forceinline__ long long c2(long long c) { return c * (c - 1) / 2; }
 
 // Adds c - 1 to pv[q] (shared) for the lanes with c > 1; lanes of one
-// in-neighbour q are consecutive in a window, so one add per run.
+// in-neighbour q are consecutive in a window, so one add per run. A window
+// that lies inside one in-neighbour's run (the usual case on long rows)
+// takes one warp reduction and one add.
 __device__ __forceinline__ void add_middle(long long *pv, int q, int c) {
-    if (!__any_sync(FULL, c > 1)) return;
-    run_add(&pv[q], q, c > 1 ? (unsigned)(c - 1) : 0u);
+    const unsigned v = c > 1 ? (unsigned)(c - 1) : 0u;
+    if (!__any_sync(FULL, v != 0)) return;
+    const int q0 = __shfl_sync(FULL, q, 0);
+    if (__all_sync(FULL, q == q0 || v == 0)) {
+        const unsigned t = __reduce_add_sync(FULL, v);
+        if (lane_id() == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&pv[q0]), (unsigned long long)t);
+        return;
+    }
+    run_add(&pv[q], q, v);
 }
 
 // Wedges u - v - w through the in-neighbour v of root u: the entries of row
