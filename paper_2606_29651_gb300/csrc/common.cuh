@@ -178,16 +178,33 @@ __device__ __forceinline__ int seg_build(SegTab &T, int st, int len, int &mypre)
 // ws + lane is found without a search: one reduction marks where non-empty
 // segments start inside the window, one ballot counts those that start
 // before it. f(valid, q, pos, col[pos]) runs on every lane (q = owning lane).
-template <int U, class F>
+// With COVER, a window that lies inside one segment (one ballot finds it)
+// skips that lookup: its elements are contiguous in the segment's row. This
+// pays where segments are long (hub rows) and costs a ballot where not.
+template <int U, bool COVER = false, class F>
 __device__ __forceinline__ void seg_visit(const int *__restrict__ col, const SegTab &T, int mypre, int mylen,
                                           int total, int wbase, int stride, F f) {
     const int lane = lane_id();
     const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const unsigned ne = COVER ? __ballot_sync(FULL, mylen > 0) : 0u;   // lanes with a segment
     for (int w0 = wbase; w0 < total; w0 += U * stride) {
         int q[U], pos[U], val[U];
 #pragma unroll
         for (int r = 0; r < U; ++r) {
             const int ws = w0 + r * stride;
+            if (COVER) {
+                // (and ends within the walk: `total` may cut a segment)
+                const unsigned cov =
+                    __ballot_sync(FULL, ws + 32 <= total && mylen > 0 && mypre <= ws && mypre + mylen >= ws + 32);
+                if (cov) {   // the segment of lane `src` holds the whole window
+                    const int src = __ffs(cov) - 1;
+                    const int rk = __popc(ne & ((1u << src) - 1u));
+                    q[r] = src;
+                    pos[r] = T.st[rk] - T.pre[rk] + ws + lane;
+                    val[r] = __ldg(col + pos[r]);
+                    continue;
+                }
+            }
             const bool starts = mylen > 0 && mypre >= ws && mypre < ws + 32;
             const unsigned sb = __reduce_or_sync(FULL, starts ? (1u << (mypre - ws)) : 0u);
             const int before = __popc(__ballot_sync(FULL, mylen > 0 && mypre < ws));

@@ -778,7 +778,7 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
             const int tot = seg_build(seg, cur, len, pre);
             const int from = (int)max(e0 - cbase, 0ll), to = (int)min(e1 - cbase, (long long)tot);
             if (from < to)
-                seg_visit<4>(g.ncol, seg, pre, len, to, from, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
+                seg_visit<4, true>(g.ncol, seg, pre, len, to, from, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
             __syncwarp();
             done(v);
             __syncwarp();

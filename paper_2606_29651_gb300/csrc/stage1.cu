@@ -224,7 +224,7 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
             }
             int mypre;
             const int total = seg_build(seg, vs, len, mypre);
-            seg_visit<4>(g.ncol, seg, mypre, len, total, wid * 32, NW * 32, [&](bool valid, int q, int pos, int w) {
+            seg_visit<4, true>(g.ncol, seg, mypre, len, total, wid * 32, NW * 32, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? out_index(hk, hv, mask, use_hash, g.ncol, s, e, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;

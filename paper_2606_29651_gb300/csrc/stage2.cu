@@ -196,7 +196,7 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
             }
             int mypre;
             const int total = seg_build(seg, vs, len, mypre);
-            seg_visit<4>(g.ncol, seg, mypre, len, total, wid * 32, NW * 32, [&](bool valid, int q, int pos, int w) {
+            seg_visit<4, true>(g.ncol, seg, mypre, len, total, wid * 32, NW * 32, [&](bool valid, int q, int pos, int w) {
                 int i = -1;
                 if (valid && w <= umax) {
                     if (use_hash) {
