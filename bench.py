@@ -73,6 +73,7 @@ def deg_class(d: np.ndarray) -> np.ndarray:
 # niorca_set_tuning): triangle roots by out-degree, 4-cycle roots by wedges.
 TRI_WARP_MAXD, TRI_CTA_MAXD, TRI_BITS_MAXD, TRI_HASH_MAXD = 64, 256, 1152, 8192
 C4_MID_MAXW, C4_CTA_MAXW = 3072, 12288
+WL_MAXD = 1024   # roots with more in-neighbours go to the key-tiled tier
 
 
 class Shape:
@@ -115,14 +116,15 @@ class Shape:
         """Relabelled ids of the roots of every 4-cycle kernel."""
         n, w = self.n, self.w_root
         live = (self.din >= 2) & (w >= 2)
+        hub = self.din > WL_MAXD   # always the key-tiled tier
         pack_lim = (1 << (32 - int(max(n - 1, 1)).bit_length())) - 2   # packed tables hold counts below this
         packed = pack_lim >= c4_warp_ub
         warp_lim = min(c4_warp_ub, 1152 if packed else 576)
         big_lim = min(c4_warp_ub, 1536 if packed else 768)
-        warp = live & (w <= warp_lim)
-        wbig = live & ~warp & (w <= big_lim)
+        warp = live & ~hub & (w <= warp_lim)
+        wbig = live & ~hub & ~warp & (w <= big_lim)
         rest = live & ~warp & ~wbig
-        team = rest & (w > C4_CTA_MAXW)
+        team = rest & ((w > C4_CTA_MAXW) | hub)
         midp = rest & ~team & (w <= 2 * C4_MID_MAXW) & (w <= pack_lim)
         mid = rest & ~team & ~midp & (w <= C4_MID_MAXW)
         cta = rest & ~team & ~midp & ~mid
@@ -637,6 +639,20 @@ def run_ours(args) -> None:
     import paper_2606_29651_gb300 as ni
 
     world, rank, local = dist_setup()
+    if args.only:
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        ni.build()
+        stream = torch.cuda.current_stream(dev)
+        timer = StepTimer(dev, stream)
+        if args.only == "rmat":
+            rec = run_rmat(ni, torch, dev, stream, timer, args.steps, args.rmat_scale,
+                           measured_peaks().get("hbm_gbs") or 6800.0)
+        else:
+            rec = {k: v for k, v in run_small_graph(ni, torch, dev, stream, timer, args.steps).items()
+                   if not k.startswith("_")}
+        print(json.dumps({"only": args.only, **rec}), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
@@ -801,6 +817,8 @@ def main() -> None:
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-max-edges", type=float, default=5e6)
     ap.add_argument("--serve-budget-gb", type=int, default=32)
+    ap.add_argument("--only", choices=["rmat", "small"],
+                    help="run one extra record alone and print it (for profiling; not the bench line)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

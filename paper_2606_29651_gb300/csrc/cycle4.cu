@@ -15,8 +15,9 @@
 // routed by their wedge count W (a count is at most W too): one warp with a
 // 6 KB table (k_c4_warp) or an 8 KB one (k_c4_warp_big), four warps
 // (k_c4_mid, packed or split tables), a 512-thread CTA (k_c4_cta), or, for the largest
-// roots, a 1024-thread CTA that counts the root's key range tile by tile in
-// shared memory (k_c4_tiled). The other tables are open-addressing hash
+// roots, and for every root with more than WL_MAXD in-neighbours, a
+// 1024-thread CTA that counts the root's key range tile by tile in shared
+// memory (k_c4_tiled). The other tables are open-addressing hash
 // tables in shared memory, either split (key and count arrays) or packed
 // (key << cb | count in one 32-bit word, cb = 32 - bits(n - 1) count bits,
 // usable while W < 2^cb - 1), which holds twice the keys in the same space.
@@ -471,22 +472,37 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
                     }
                     W = warp_sum(rc.len0 + rc.len1);
                 }
+            } else if (din <= WL_MAXD) {
+                for (int p = lane; p < din; p += 32) W += g.wl[b + p].y;
+                W = warp_sum(W);
             } else {
-                for (int p = lane; p < din; p += 32) W += wedge_seg(g, u, din, b + p).y;
+                // more in-neighbours than the wedge-segment table covers: the
+                // key-tiled tier, which takes any root, without searching every
+                // row for W here (one warp for a hub's rows would be the
+                // kernel's tail); its order takes the in-neighbours' degree
+                // sum, at least W, in W's place
+#pragma unroll 8
+                for (int p = lane; p < din; p += 32) {
+                    const int4 rv = g.rinfo[g.ncol[b + p]];
+                    W += rv.z - rv.x;
+                }
                 W = warp_sum(W);
             }
-            if (W < 2) return;
-            if (W > here_lim) {
+            const bool hub = din > WL_MAXD;
+            if (W < 2 && !hub) return;
+            if (W > here_lim || hub) {
                 if (lane == 0) {
                     int which, list;   // queue counter and list slot (lists + list * n)
-                    if (!BIG && W <= big_lim) { which = CNT_C4_WBIG; list = CW_BIG_LIST; }
+                    if (hub) { which = CNT_C4_TEAM; list = 4; }
+                    else if (!BIG && W <= big_lim) { which = CNT_C4_WBIG; list = CW_BIG_LIST; }
                     else if (W > teamw) { which = CNT_C4_TEAM; list = 4; }
                     else if (W <= 2 * CM_MAXW && W <= pack_lim) { which = CNT_C4_MIDP; list = 5; }
                     else if (W <= CM_MAXW) { which = CNT_C4_MID; list = 2; }
                     else { which = CNT_C4_CTA; list = 3; }
                     const int at = atomicAdd(&counters[which], 1);
                     lists[(size_t)list * g.n + at] = u;
-                    if (which == CNT_C4_TEAM) lists[(size_t)g.n + at] = (int)W;   // the order of the key-tiled tier
+                    if (which == CNT_C4_TEAM)   // the order of the key-tiled tier
+                        lists[(size_t)g.n + at] = (int)(W < 0x7fffffffll ? W : 0x7fffffffll);
                 }
                 return;
             }
