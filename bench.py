@@ -648,6 +648,9 @@ def run_ours(args) -> None:
         if args.only == "rmat":
             rec = run_rmat(ni, torch, dev, stream, timer, args.steps, args.rmat_scale,
                            measured_peaks().get("hbm_gbs") or 6800.0)
+        elif args.only == "batched":
+            rec = {k: v for k, v in run_batched(ni, torch, dev, stream, timer, args.steps, args.batch_graphs).items()
+                   if not k.startswith("_")}
         else:
             rec = {k: v for k, v in run_small_graph(ni, torch, dev, stream, timer, args.steps).items()
                    if not k.startswith("_")}
@@ -817,7 +820,7 @@ def main() -> None:
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-max-edges", type=float, default=5e6)
     ap.add_argument("--serve-budget-gb", type=int, default=32)
-    ap.add_argument("--only", choices=["rmat", "small"],
+    ap.add_argument("--only", choices=["rmat", "small", "batched"],
                     help="run one extra record alone and print it (for profiling; not the bench line)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -224,6 +224,40 @@ __device__ __forceinline__ void seg_visit(const int *__restrict__ col, const Seg
     }
 }
 
+// seg_visit for consecutive windows (stride 32) from wbase: a round of U
+// windows takes its segment starts from one lane value (the start relative
+// to the round), and the number of segments that start before a window is
+// carried from the window before instead of counted by a ballot.
+template <int U, class F>
+__device__ __forceinline__ void seg_visit32(const int *__restrict__ col, const SegTab &T, int mypre, int mylen,
+                                            int total, int wbase, F f) {
+    const int lane = lane_id();
+    const unsigned le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    int before = __popc(__ballot_sync(FULL, mylen > 0 && mypre < wbase));   // segments before the window
+    for (int w0 = wbase; w0 < total; w0 += U * 32) {
+        const int rel = mylen > 0 ? mypre - w0 : -1;   // this lane's segment start within the round
+        const bool in_round = (unsigned)rel < (unsigned)(U * 32);
+        int q[U], pos[U], val[U];
+#pragma unroll
+        for (int r = 0; r < U; ++r) {
+            const unsigned sb = __reduce_or_sync(FULL, in_round && (rel >> 5) == r ? 1u << (rel & 31) : 0u);
+            const int k = w0 + 32 * r + lane;
+            q[r] = 0;
+            pos[r] = -1;
+            val[r] = 0;
+            if (k < total) {
+                const int rk = before + __popc(sb & le) - 1;
+                q[r] = T.idx[rk];
+                pos[r] = T.st[rk] + (k - T.pre[rk]);
+                val[r] = __ldg(col + pos[r]);
+            }
+            before += __popc(sb);
+        }
+#pragma unroll
+        for (int r = 0; r < U; ++r) f(pos[r] >= 0, q[r], pos[r], val[r]);
+    }
+}
+
 // First position p in [lo, hi) with a[p] >= key (a sorted ascending).
 __device__ __forceinline__ int lower_bound(const int *a, int lo, int hi, int key) {
     while (lo < hi) {

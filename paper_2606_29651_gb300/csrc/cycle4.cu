@@ -32,7 +32,7 @@ constexpr int CW_WARPS = 4;
 constexpr int CW_WORDS = 1536;      // table words per warp of k_c4_warp: 6 KB, 8 CTAs of 4 warps per SM
 constexpr int CWB_WORDS = 2048;     // k_c4_warp_big: 8 KB, 6 CTAs per SM
 constexpr int CW_MAXW = 1536;       // largest W of a root in the warp tiers
-constexpr int CW_DUPS = 32;         // repeated keys a warp credits without a second walk
+constexpr int CW_DUPS = 32;         // repeated keys a warp credits by search at most
 constexpr int CW_BIG_LIST = 0;      // list slot of k_c4_warp_big's roots: the triangle stage's heavy list,
                                     // which nothing reads after that stage
 constexpr int CM_THREADS = 128;
@@ -82,6 +82,7 @@ __device__ __forceinline__ int2 wedge_seg(const Graph &g, int u, int din, int p)
 // each entry, made here with every thread independent, so that the
 // per-root kernels read one coalesced 8-byte entry per in-neighbour.
 __global__ void __launch_bounds__(256, 8) k_c4_wedge_len(Graph g, int2 *wl, const int *counters) {
+    pdl_begin();
     if (degree_overflow(counters)) return;
     const int hl = threadIdx.x & 15;
     const int gh = (blockIdx.x * blockDim.x + threadIdx.x) >> 4, nh = (gridDim.x * blockDim.x) >> 4;
@@ -151,7 +152,7 @@ __device__ __forceinline__ void walk_wedges(const Graph &g, int u, int b, int di
     for (int c = 0; 32 * c < din; ++c) {
         int v, len, pre;
         const int total = root_chunk(g, u, b, din, c, T, rc, v, len, pre);
-        seg_visit<4>(g.ncol, T, pre, len, total, 0, 32, [&](bool ok, int q, int, int w) { f(ok, q, w); });
+        seg_visit32<4>(g.ncol, T, pre, len, total, 0, [&](bool ok, int q, int, int w) { f(ok, q, w); });
         __syncwarp();
         done(v);
         __syncwarp();
@@ -278,7 +279,8 @@ struct PackedTab {
 template <bool CTA, class Tab>
 __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b, int din,
                                         const Tab &T, int wid, int nw, int tid, int nthreads, SegTab &seg,
-                                        long long *pv, int *flags, const RootChunks &rc = RootChunks{}) {
+                                        long long *pv, int *flags, const RootChunks &rc = RootChunks{},
+                                        long long W = 0) {
     const int lane = lane_id();
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
@@ -311,7 +313,10 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         // A warp sweeps its table for the repeated keys (count >= 2), credits
         // them, and lists up to CW_DUPS of them in flags[]; the middle
         // vertices of key w are N-(u) ∩ N(w), found by searching row w for
-        // each in-neighbour. More repeated keys: the middle walk below.
+        // each in-neighbour (one search per lane and pair), while the pairs
+        // number at most W / 4: each search is a short chain of dependent
+        // loads, and a root of a small dense graph with tens of repeated keys
+        // walks its few windows again sooner. Otherwise: the middle walk below.
         long long su = 0;
         int nd = 0;
         for (int i0 = 0; i0 < nt; i0 += 32) {   // all lanes take part in every ballot
@@ -333,14 +338,14 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
         su = warp_sum(su);
         if (lane == 0) add64(&vacc[u].C4, su);
         __syncwarp();
-        if (nd <= CW_DUPS) {
-            for (int k = 0; k < nd; ++k) {
+        if (nd <= CW_DUPS && (long long)nd * din * 4 <= W) {
+            // one (key, in-neighbour) pair per lane, all searches independent
+            for (int t = lane; t < nd * din; t += 32) {
+                const int k = t / din, p = t - k * din;
                 const int w = flags[k], c = flags[CW_DUPS + k];
                 const int4 rw = g.rinfo[w];
-                for (int ch = 0, p = lane; p < din; ++ch, p += 32) {
-                    const int v = ch < rc.have ? (ch == 0 ? rc.v0 : rc.v1) : g.ncol[b + p];
-                    if (find_sorted(g.ncol, rw.x, rw.z, v) >= 0) add64(&vacc[v].C4, c - 1);
-                }
+                const int v = g.ncol[b + p];
+                if (find_sorted(g.ncol, rw.x, rw.z, v) >= 0) add64(&vacc[v].C4, c - 1);
             }
             __syncwarp();
         } else {
@@ -454,7 +459,7 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
             long long W = 0;   // exact wedge count W of root u
             RootChunks rc;
             if (din <= 64) {   // both chunks' segments stay in registers
-                rc.v0 = lane < din ? g.ncol[b + lane] : -1;   // read only for the credits of repeated keys
+                rc.v0 = lane < din ? g.ncol[b + lane] : -1;   // for the middle walk's credits
                 rc.st0 = s0.x;
                 rc.len0 = s0.y;
                 if (din <= 32) {   // one chunk: its segment table gives W
@@ -511,10 +516,10 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
             slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > (unsigned)TS ? (unsigned)TS : slots);
             if constexpr (SPLIT) {
                 const SplitTab T{sk, sc, slots, nullptr};
-                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc);
+                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc, W);
             } else {
                 const PackedTab T{S.t, slots, cb, nullptr};
-                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc);
+                c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc, W);
             }
         }();
         u = un;
@@ -528,21 +533,25 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
 // 8 CTAs of 4 warps per SM: 6 KB tables and at most 64 registers a thread.
 __global__ void __launch_bounds__(CW_WARPS * 32, 8) k_c4_warp(Graph g, VAcc *vacc, int *lists, int *counters,
                                                               int maxw, int cb, int teamw) {
+    pdl_begin();
     c4_warp_body<false, false>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
 __global__ void __launch_bounds__(CW_WARPS * 32, 8) k_c4_warp_split(Graph g, VAcc *vacc, int *lists,
                                                                     int *counters, int maxw, int cb, int teamw) {
+    pdl_begin();
     c4_warp_body<true, false>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_big(Graph g, VAcc *vacc, int *lists, int *counters,
                                                                int maxw, int cb, int teamw) {
+    pdl_begin();
     c4_warp_body<false, true>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
 __global__ void __launch_bounds__(CW_WARPS * 32) k_c4_warp_big_split(Graph g, VAcc *vacc, int *lists,
                                                                      int *counters, int maxw, int cb, int teamw) {
+    pdl_begin();
     c4_warp_body<true, true>(g, vacc, lists, counters, maxw, cb, teamw);
 }
 
@@ -593,6 +602,7 @@ constexpr size_t CC_SMEM = cq_smem(CC_THREADS, CC_SLOTS, CC_MAXW);
 // enough count bits), then the split one (W <= 3072).
 __global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, const int *lists, int *counters,
                                                        int cb) {
+    pdl_begin();
     if (degree_overflow(counters)) return;
     c4_queue<CM_THREADS, CM_SLOTS, CM_MAXW, true>(g, vacc, lists + 5 * (size_t)g.n, counters[CNT_C4_MIDP],
                                                   counters + CNT_C4_MIDP_NEXT, cb);
@@ -602,6 +612,7 @@ __global__ void __launch_bounds__(CM_THREADS) k_c4_mid(Graph g, VAcc *vacc, cons
 
 __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, const int *lists, int *counters,
                                                        int cb) {
+    pdl_begin();
     if (degree_overflow(counters)) return;
     c4_queue<CC_THREADS, CC_SLOTS, CC_MAXW, false>(g, vacc, lists + 3 * (size_t)g.n, counters[CNT_C4_CTA],
                                                    counters + CNT_C4_CTA_NEXT, cb);
@@ -644,6 +655,7 @@ static_assert(CK_SMEM <= 227 * 1024, "k_c4_tiled shared memory");
 // octave) into list 0, and the prefix sums of their in-degrees (the offsets
 // of their cursors) into list 2. One CTA.
 __global__ void __launch_bounds__(1024) k_c4_tiled_plan(Graph g, int *lists, int *counters) {
+    pdl_begin();
     __shared__ int hist[64], base[64];
     __shared__ int wsum[32];
     if (degree_overflow(counters)) return;
@@ -901,6 +913,7 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
 // more (only for a CSR that is not symmetric) stops with ENOTSIMPLE.
 __global__ void __launch_bounds__(CK_THREADS) k_c4_tiled(Graph g, VAcc *vacc, const int *lists, int *counters,
                                                          int4 *cursors, long long cap, int *status) {
+    pdl_begin();
     extern __shared__ __align__(16) unsigned char dsm[];
     unsigned *cnt = reinterpret_cast<unsigned *>(dsm);
     SegTab *segs = reinterpret_cast<SegTab *>(cnt + CK_WORDS);
@@ -943,7 +956,7 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     // the wedge segments take the region of the triangle counts, dead after the aggregate stage
     int2 *wl = reinterpret_cast<int2 *>(w.tcnt);
     Graph g{w.n, w.m, w.rinfo, w.ncol, wl};
-    k_c4_wedge_len<<<w.num_sms * 8, 256, 0, st>>>(g, wl, w.counters);
+    launch_pdl(k_c4_wedge_len, w.num_sms * 8, 256, 0, st, g, wl, w.counters);
     after_launch(st, K_C4_WEDGE_LEN);
     const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
     const int cb = packed_count_bits(w.n);
@@ -957,29 +970,29 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     static const int occ_b = resident_ctas((const void *)k_c4_warp_big, CW_WARPS * 32, 0);
     static const int occ_bs = resident_ctas((const void *)k_c4_warp_big_split, CW_WARPS * 32, 0);
     if (packed)
-        k_c4_warp<<<w.num_sms * min(w.tune[TUNE_GRID_C4], occ_w), CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw,
+        launch_pdl(k_c4_warp, w.num_sms * min(w.tune[TUNE_GRID_C4], occ_w), CW_WARPS * 32, 0, st, g, w.vacc, w.lists, w.counters, maxw,
                                                                              cb, teamw);
     else
-        k_c4_warp_split<<<w.num_sms * min(w.tune[TUNE_GRID_C4], occ_ws), CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters,
+        launch_pdl(k_c4_warp_split, w.num_sms * min(w.tune[TUNE_GRID_C4], occ_ws), CW_WARPS * 32, 0, st, g, w.vacc, w.lists, w.counters,
                                                                                    maxw, cb, teamw);
     after_launch(st, K_C4_WARP);
     // roots k_c4_warp queued for the 8 KB tables: one resident wave
     if (packed)
-        k_c4_warp_big<<<w.num_sms * occ_b, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb, teamw);
+        launch_pdl(k_c4_warp_big, w.num_sms * occ_b, CW_WARPS * 32, 0, st, g, w.vacc, w.lists, w.counters, maxw, cb, teamw);
     else
-        k_c4_warp_big_split<<<w.num_sms * occ_bs, CW_WARPS * 32, 0, st>>>(g, w.vacc, w.lists, w.counters, maxw, cb,
+        launch_pdl(k_c4_warp_big_split, w.num_sms * occ_bs, CW_WARPS * 32, 0, st, g, w.vacc, w.lists, w.counters, maxw, cb,
                                                                      teamw);
     after_launch(st, K_C4_WARP_BIG);
     static const int occ_m = resident_ctas((const void *)k_c4_mid, CM_THREADS, CM_SMEM);
     static const int occ_c = resident_ctas((const void *)k_c4_cta, CC_THREADS, CC_SMEM);
-    k_c4_mid<<<w.num_sms * occ_m, CM_THREADS, CM_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    launch_pdl(k_c4_mid, w.num_sms * occ_m, CM_THREADS, CM_SMEM, st, g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_MID);
-    k_c4_cta<<<w.num_sms * occ_c, CC_THREADS, CC_SMEM, st>>>(g, w.vacc, w.lists, w.counters, cb);
+    launch_pdl(k_c4_cta, w.num_sms * occ_c, CC_THREADS, CC_SMEM, st, g, w.vacc, w.lists, w.counters, cb);
     after_launch(st, K_C4_CTA);
-    k_c4_tiled_plan<<<1, 1024, 0, st>>>(g, w.lists, w.counters);
+    launch_pdl(k_c4_tiled_plan, 1, 1024, 0, st, g, w.lists, w.counters);
     after_launch(st, K_C4_PLAN);
     static const int occ_t = resident_ctas((const void *)k_c4_tiled, CK_THREADS, CK_SMEM);
-    k_c4_tiled<<<w.num_sms * occ_t, CK_THREADS, CK_SMEM, st>>>(g, w.vacc, w.lists, w.counters,
+    launch_pdl(k_c4_tiled, w.num_sms * occ_t, CK_THREADS, CK_SMEM, st, g, w.vacc, w.lists, w.counters,
                                                       reinterpret_cast<int4 *>(w.tcnt), (long long)w.m / 2,
                                                       w.status);
     after_launch(st, K_C4_TILED);

@@ -67,6 +67,31 @@ __device__ __forceinline__ int cta_next(int *ctr) {
     return s_item;
 }
 
+// Programmatic dependent launch: every kernel of the library is launched
+// with launch_pdl, so that the next kernel on the stream is set up while
+// the CTAs of the one before it drain (which hides most of the launch gap
+// between the short kernels of a small graph), and begins with pdl_begin:
+// it waits until the kernel before it has completed and its writes are
+// visible, before touching memory. No kernel triggers its dependents early:
+// CTAs of the next kernel waiting on SMs from the start of a kernel made
+// the ER n = 1e6 call 35% slower.
+__device__ __forceinline__ void pdl_begin() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <class... P, class... A>
+void launch_pdl(void (*kernel)(P...), unsigned grid, unsigned threads, size_t smem, cudaStream_t st, A... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
+
 // CTAs of `kernel` (launched with `threads` threads and `smem` bytes of
 // dynamic shared memory) that one SM holds at once: the size of a
 // persistent grid is SMs times this.

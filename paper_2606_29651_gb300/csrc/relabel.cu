@@ -41,6 +41,7 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *wsum, int *total
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int *in, long long len, int *part) {
+    pdl_begin();
     __shared__ int wsum[32];
     __shared__ int tot;
     const long long base = (long long)blockIdx.x * SCAN_TILE;
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int *in, lon
 }
 
 __global__ void __launch_bounds__(1024) k_scan_top(int *part, int nblocks) {
+    pdl_begin();
     __shared__ int wsum[32];
     __shared__ int tot;
     int carry = 0;
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(1024) k_scan_top(int *part, int nblocks) {
 // With part == nullptr a single block scans the whole array (len <= SCAN_TILE).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int *in, int *out, long long len, const int *part,
                                                            int write_total) {
+    pdl_begin();
     __shared__ int tile[SCAN_TILE];
     __shared__ int wsum[32];
     __shared__ int tot;
@@ -109,15 +112,15 @@ void launch_exclusive_scan(const int *in, int *out, long long len, bool write_to
         return;
     }
     if (nb == 1) {   // one tile: one launch
-        k_scan_down<<<1, SCAN_THREADS, 0, st>>>(in, out, len, nullptr, write_total ? 1 : 0);
+        launch_pdl(k_scan_down, 1, SCAN_THREADS, 0, st, in, out, len, nullptr, write_total ? 1 : 0);
         after_launch(st, K_SCAN);
         return;
     }
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, len, part);
+    launch_pdl(k_scan_reduce, nb, SCAN_THREADS, 0, st, in, len, part);
     after_launch(st, K_SCAN);
-    k_scan_top<<<1, 1024, 0, st>>>(part, nb);
+    launch_pdl(k_scan_top, 1, 1024, 0, st, part, nb);
     after_launch(st, K_SCAN);
-    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, out, len, part, write_total ? 1 : 0);
+    launch_pdl(k_scan_down, nb, SCAN_THREADS, 0, st, in, out, len, part, write_total ? 1 : 0);
     after_launch(st, K_SCAN);
 }
 
@@ -128,6 +131,7 @@ constexpr int RL_THREADS = 256;
 // Degrees (with offset validation) and the class histogram of each tile.
 __global__ void __launch_bounds__(RL_THREADS) k_class_hist(const int *rowptr, int n, int m, int2 *vinfo, int *chist,
                                                            int ntiles, int *counters, int *status) {
+    pdl_begin();
     __shared__ int h[NCLASS];
     __shared__ int smax;
     for (int c = threadIdx.x; c < NCLASS; c += RL_THREADS) h[c] = 0;
@@ -160,6 +164,7 @@ __global__ void __launch_bounds__(RL_THREADS) k_class_hist(const int *rowptr, in
 // New id of every vertex: class offset + stable rank by old id within class.
 __global__ void __launch_bounds__(RL_THREADS) k_class_scatter(int n, int2 *vinfo, const int *coff, int ntiles,
                                                               int *perm, int *ndeg) {
+    pdl_begin();
     constexpr int NW = RL_THREADS / 32;
     __shared__ int run[NCLASS];
     __shared__ int tot[NCLASS];
@@ -222,6 +227,7 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
                                                            const int *nrow, const int *coff, int ntiles, int *ncol,
                                                            int4 *rinfo, VAcc *vacc, int *tcnt, int *status,
                                                            int long_class) {
+    pdl_begin();
     __shared__ int hist_all[8][NCLASS];
     const int lane = lane_id();
     int *H = hist_all[threadIdx.x >> 5];
@@ -320,6 +326,7 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
                                                                   const int *nrow, const int *coff, int ntiles,
                                                                   int *ncol, int4 *rinfo, VAcc *vacc, int *tcnt,
                                                                   int *status, int long_class) {
+    pdl_begin();
     constexpr int NW = RLC_THREADS / 32;
     __shared__ int H[NCLASS];
     __shared__ int tot[NCLASS];
@@ -410,21 +417,21 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
 
 static void relabel_common(const int *rowptr, const int *colidx, const int2 *vrange, Work &w, cudaStream_t st) {
     const int nt = w.ntiles;
-    k_class_hist<<<nt, RL_THREADS, 0, st>>>(rowptr, w.n, w.m, w.vinfo, w.chist, nt, w.counters, w.status);
+    launch_pdl(k_class_hist, nt, RL_THREADS, 0, st, rowptr, w.n, w.m, w.vinfo, w.chist, nt, w.counters, w.status);
     after_launch(st, K_CLASS_HIST);
     launch_exclusive_scan(w.chist, w.coff, (long long)NCLASS * nt, false, w.scan_part, st);
     // ndeg (degree of each new id) is staged in `split`, then scanned into nrow
-    k_class_scatter<<<nt, RL_THREADS, 0, st>>>(w.n, w.vinfo, w.coff, nt, w.perm, w.split);
+    launch_pdl(k_class_scatter, nt, RL_THREADS, 0, st, w.n, w.vinfo, w.coff, nt, w.perm, w.split);
     after_launch(st, K_CLASS_SCATTER);
     launch_exclusive_scan(w.split, w.nrow, w.n, true, w.scan_part, st);
     const int lrc = w.tune[TUNE_LONG_ROW_CLASS];
     // more CTAs than an SM holds: with rows of uneven length, the later
     // waves act as load balancing
-    k_relabel_rows_warp<<<w.num_sms * w.tune[TUNE_GRID_RELABEL], 256, 0, st>>>(
+    launch_pdl(k_relabel_rows_warp, w.num_sms * w.tune[TUNE_GRID_RELABEL], 256, 0, st,
         rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow, w.coff, nt, w.ncol, w.rinfo, w.vacc, w.tcnt, w.status,
         lrc);
     after_launch(st, K_RELABEL_WARP);
-    k_relabel_rows_cta<<<w.num_sms * 2, RLC_THREADS, 0, st>>>(rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow,
+    launch_pdl(k_relabel_rows_cta, w.num_sms * 2, RLC_THREADS, 0, st, rowptr, colidx, w.n, vrange, w.vinfo, w.perm, w.nrow,
                                                               w.coff, nt, w.ncol, w.rinfo, w.vacc, w.tcnt,
                                                               w.status, lrc);
     after_launch(st, K_RELABEL_CTA);
@@ -442,6 +449,7 @@ void launch_relabel_batch(const int *rowptr, const int *colidx, const int2 *vran
 // consistency of the offsets with rowptr.
 __global__ void k_batch_setup(const int *rowptr, const long long *vo, const long long *eo, int G, int total_n,
                               int2 *vrange, int *status) {
+    pdl_begin();
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
     int bad = 0;
@@ -466,7 +474,7 @@ __global__ void k_batch_setup(const int *rowptr, const long long *vo, const long
 
 void launch_batch_setup(const int *rowptr, const long long *vtx_offset, const long long *edge_offset, int num_graphs,
                         int total_n, int2 *vrange, int *status, int num_sms, cudaStream_t st) {
-    k_batch_setup<<<num_sms * 4, 256, 0, st>>>(rowptr, vtx_offset, edge_offset, num_graphs, total_n, vrange, status);
+    launch_pdl(k_batch_setup, num_sms * 4, 256, 0, st, rowptr, vtx_offset, edge_offset, num_graphs, total_n, vrange, status);
     after_launch(st, K_BATCH_SETUP);
 }
 

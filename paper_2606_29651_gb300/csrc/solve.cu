@@ -83,7 +83,8 @@ __device__ __forceinline__ void to_induced(long long *p) {
 // each of the 32 in turn (coalesced gathers, two vertices in flight), each
 // lane solves its own vertex, and the warp writes the group's 32 output rows
 // (3840 contiguous bytes) with coalesced stores through shared memory, which
-// also suits an output buffer in host memory.
+// also suits an output buffer in host memory. With long_class 0 (a graph
+// with fewer vertices than the grid has warps) every vertex takes a warp.
 __device__ __forceinline__ void solve_write(long long d, const VAcc &a, long long sS1, long long sA1, int induced,
                                             long long *o) {
     long long psi[15];
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(Graph g, const VAcc 
                                                             const int2 *vinfo, long long *out, int induced,
                                                             const int *coff, int ntiles, int long_class,
                                                             const int *counters) {
+    pdl_begin();
     __shared__ long long obuf[SOLVE_WARPS][32 * 15];
     if (degree_overflow(counters)) return;
     const int lane = lane_id();
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(Graph g, const VAcc 
         sA1 = warp_sum(sA1);
         if (lane == 0) solve_write(rx.z - rx.x, vacc[x], sS1, sA1, induced, out + (size_t)perm[x] * 15);
     }
-    for (int xo0 = gw * 32; xo0 < g.n; xo0 += nw * 32) {
+    for (int xo0 = gw * 32; long_class > 0 && xo0 < g.n; xo0 += nw * 32) {
         const int xo = xo0 + lane;   // caller id
         int x = -1;                  // relabelled id, if this group solves it
         if (xo < g.n) {
@@ -170,14 +172,19 @@ __global__ void __launch_bounds__(SOLVE_WARPS * 32) k_solve(Graph g, const VAcc 
 
 void launch_solve(Work &w, long long *out, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol};
-    k_solve<<<w.num_sms * w.tune[TUNE_GRID_SOLVE], SOLVE_WARPS * 32, 0, st>>>(
-        g, w.vacc, w.perm, w.vinfo, out, w.induced, w.coff, w.ntiles, w.tune[TUNE_LONG_ROW_CLASS], w.counters);
+    const int grid = w.num_sms * w.tune[TUNE_GRID_SOLVE];
+    // a graph with no more vertices than the grid has warps: one warp per
+    // vertex (long_class 0), so that no warp solves 32 vertices in turn
+    const int lc = (long long)w.n <= (long long)grid * SOLVE_WARPS ? 0 : w.tune[TUNE_LONG_ROW_CLASS];
+    launch_pdl(k_solve, grid, SOLVE_WARPS * 32, 0, st,
+        g, w.vacc, w.perm, w.vinfo, out, w.induced, w.coff, w.ntiles, lc, w.counters);
     after_launch(st, K_SOLVE);
 }
 
 // Full simple-graph check: offsets, strictly increasing rows, no self-loops,
 // and symmetry (every (x, y) has its (y, x)), one warp per row.
 __global__ void __launch_bounds__(256) k_validate(const int *rowptr, const int *colidx, int n, int m, int *status) {
+    pdl_begin();
     const int lane = lane_id();
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -203,7 +210,7 @@ __global__ void __launch_bounds__(256) k_validate(const int *rowptr, const int *
 
 void launch_validate(const int *rowptr, const int *colidx, int n, int m, int *status, int num_sms, cudaStream_t st) {
     if (n <= 0) return;
-    k_validate<<<num_sms * 8, 256, 0, st>>>(rowptr, colidx, n, m, status);
+    launch_pdl(k_validate, num_sms * 8, 256, 0, st, rowptr, colidx, n, m, status);
     after_launch(st, K_VALIDATE);
 }
 

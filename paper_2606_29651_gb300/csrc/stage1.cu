@@ -41,6 +41,7 @@ struct __align__(16) TriWarpSmem {
 
 __global__ void __launch_bounds__(TW_WARPS * 32, 8) k_tri_warp(Graph g, int *tcnt, VAcc *vacc, int *heavy,
                                                             int *counters, int maxd) {
+    pdl_begin();
     __shared__ TriWarpSmem sm_all[TW_WARPS];
     TriWarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(TW_WARPS * 32, 8) k_tri_warp(Graph g, int *tcn
             }
             int mypre;
             const int total = seg_build(S.seg, vs, len, mypre);
-            seg_visit<2>(g.ncol, S.seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            seg_visit32<2>(g.ncol, S.seg, mypre, len, total, 0, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? hset_find(S.hk, S.hv, mask, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
@@ -355,6 +356,7 @@ __device__ __forceinline__ void tri_cta(const Graph &g, int *tcnt, VAcc *vacc, c
 
 __global__ void __launch_bounds__(TS_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
                                                         int *counters, int bits_maxd, int hash_maxd) {
+    pdl_begin();
     if (degree_overflow(counters)) return;
     tri_cta<TS_THREADS, TS_MAXD, 4 * TS_MAXD, TS_MAXD, false, 4>(g, tcnt, vacc, heavy, counters[CNT_TRI_HEAVY],
                                                             counters + CNT_TRI_CTA_NEXT, bits_maxd, hash_maxd);
@@ -362,6 +364,7 @@ __global__ void __launch_bounds__(TS_THREADS) k_tri_cta(Graph g, int *tcnt, VAcc
 
 __global__ void __launch_bounds__(TB_THREADS) k_tri_big(Graph g, int *tcnt, VAcc *vacc, const int *heavy,
                                                         int *counters, int bits_maxd, int hash_maxd) {
+    pdl_begin();
     if (degree_overflow(counters)) return;
     tri_cta<TB_THREADS, TB_BITMAT_MAXD, TB_BITMAT_HSLOTS, TB_HASH_MAXD, true, 4>(g, tcnt, vacc, heavy,
                                                                             counters[CNT_TRI_BIG],
@@ -376,13 +379,13 @@ void launch_stage1(Work &w, cudaStream_t st) {
     static const int occ_w = resident_ctas((const void *)k_tri_warp, TW_WARPS * 32, 0);
     static const int occ_c = resident_ctas((const void *)k_tri_cta, TS_THREADS, TS_SMEM);
     static const int occ_b = resident_ctas((const void *)k_tri_big, TB_THREADS, TB_SMEM);
-    k_tri_warp<<<w.num_sms * min(w.tune[TUNE_GRID_TRI], occ_w), TW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, w.lists,
+    launch_pdl(k_tri_warp, w.num_sms * min(w.tune[TUNE_GRID_TRI], occ_w), TW_WARPS * 32, 0, st, g, w.tcnt, w.vacc, w.lists,
                                                                                        w.counters, maxd);
     after_launch(st, K_TRI_WARP);
     const int bits = w.tune[TUNE_TRI_BITS_MAXD], hash = w.tune[TUNE_TRI_HASH_MAXD];
-    k_tri_cta<<<w.num_sms * occ_c, TS_THREADS, TS_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
+    launch_pdl(k_tri_cta, w.num_sms * occ_c, TS_THREADS, TS_SMEM, st, g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
     after_launch(st, K_TRI_CTA);
-    k_tri_big<<<w.num_sms * occ_b, TB_THREADS, TB_SMEM, st>>>(g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
+    launch_pdl(k_tri_big, w.num_sms * occ_b, TB_THREADS, TB_SMEM, st, g, w.tcnt, w.vacc, w.lists, w.counters, bits, hash);
     after_launch(st, K_TRI_BIG);
 }
 

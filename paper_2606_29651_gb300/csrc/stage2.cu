@@ -59,6 +59,7 @@ __device__ __forceinline__ bool edge_aggregates(const Graph &g, const int *tcnt,
 
 __global__ void __launch_bounds__(AW_WARPS * 32, 8) k_agg_warp(Graph g, const int *tcnt, VAcc *vacc, int *heavy,
                                                             int *counters, int maxd) {
+    pdl_begin();
     __shared__ AggWarpSmem sm_all[AW_WARPS];
     AggWarpSmem &S = sm_all[threadIdx.x >> 5];
     const int lane = lane_id();
@@ -95,7 +96,7 @@ __global__ void __launch_bounds__(AW_WARPS * 32, 8) k_agg_warp(Graph g, const in
             }
             int mypre;
             const int total = seg_build(S.seg, vs, len, mypre);
-            seg_visit<2>(g.ncol, S.seg, mypre, len, total, 0, 32, [&](bool valid, int q, int pos, int w) {
+            seg_visit32<2>(g.ncol, S.seg, mypre, len, total, 0, [&](bool valid, int q, int pos, int w) {
                 const int i = (valid && w <= umax) ? hset_find(S.hk, S.hv, mask, w) : -1;
                 const bool hit = i >= 0;
                 if (!__any_sync(FULL, hit)) return;
@@ -270,6 +271,7 @@ __device__ __forceinline__ void agg_cta(const Graph &g, const int *tcnt, VAcc *v
 
 __global__ void __launch_bounds__(AS_THREADS) k_agg_cta(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
                                                         int *counters, int bits_maxd, int hash_maxd) {
+    pdl_begin();
     if (degree_overflow(counters)) return;
     agg_cta<AS_THREADS, AS_MAXD, 4 * AS_MAXD, AS_MAXD, false, 4>(g, tcnt, vacc, heavy, counters[CNT_AGG_HEAVY],
                                                             counters + CNT_AGG_CTA_NEXT, bits_maxd, hash_maxd);
@@ -277,6 +279,7 @@ __global__ void __launch_bounds__(AS_THREADS) k_agg_cta(Graph g, const int *tcnt
 
 __global__ void __launch_bounds__(AB_THREADS) k_agg_big(Graph g, const int *tcnt, VAcc *vacc, const int *heavy,
                                                         int *counters, int bits_maxd, int hash_maxd) {
+    pdl_begin();
     if (degree_overflow(counters)) return;
     agg_cta<AB_THREADS, AB_BITMAT_MAXD, AB_BITMAT_HSLOTS, AB_HASH_MAXD, true, 4>(g, tcnt, vacc, heavy,
                                                                             counters[CNT_AGG_BIG],
@@ -291,13 +294,13 @@ void launch_stage2(Work &w, cudaStream_t st) {
     static const int occ_w = resident_ctas((const void *)k_agg_warp, AW_WARPS * 32, 0);
     static const int occ_c = resident_ctas((const void *)k_agg_cta, AS_THREADS, AS_SMEM);
     static const int occ_b = resident_ctas((const void *)k_agg_big, AB_THREADS, AB_SMEM);
-    k_agg_warp<<<w.num_sms * min(w.tune[TUNE_GRID_AGG], occ_w), AW_WARPS * 32, 0, st>>>(g, w.tcnt, w.vacc, heavy,
+    launch_pdl(k_agg_warp, w.num_sms * min(w.tune[TUNE_GRID_AGG], occ_w), AW_WARPS * 32, 0, st, g, w.tcnt, w.vacc, heavy,
                                                                                        w.counters, maxd);
     after_launch(st, K_AGG_WARP);
     const int bits = w.tune[TUNE_TRI_BITS_MAXD], hash = w.tune[TUNE_TRI_HASH_MAXD];
-    k_agg_cta<<<w.num_sms * occ_c, AS_THREADS, AS_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
+    launch_pdl(k_agg_cta, w.num_sms * occ_c, AS_THREADS, AS_SMEM, st, g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
     after_launch(st, K_AGG_CTA);
-    k_agg_big<<<w.num_sms * occ_b, AB_THREADS, AB_SMEM, st>>>(g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
+    launch_pdl(k_agg_big, w.num_sms * occ_b, AB_THREADS, AB_SMEM, st, g, w.tcnt, w.vacc, heavy, w.counters, bits, hash);
     after_launch(st, K_AGG_BIG);
 }
 
