@@ -272,8 +272,7 @@ struct PackedTab {
 // A repeated key is a 4-cycle, so roots without one skip the credit and
 // middle passes. A CTA records the slots it fills in `touched` (flags[0]
 // counts them, flags[1] notes a repeated key) and empties only those; a warp
-// keeps no list: its table is sized to the root (at least twice W slots),
-// and it sweeps that region.
+// keeps no list: it uses its whole table for every root and sweeps it.
 // pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
 // the CTA).
 template <bool CTA, class Tab>
@@ -394,7 +393,6 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     sync();
 }
 
-constexpr int CW_MIN_SLOTS = 64;
 
 template <int WORDS>
 struct __align__(16) C4WarpSmem {
@@ -511,9 +509,11 @@ __device__ __forceinline__ void c4_warp_body(Graph g, VAcc *vacc, int *lists, in
                 }
                 return;
             }
-            // at least 2W slots (W <= half the table), else the whole table (W <= 3/4 of it)
-            unsigned slots = next_pow2(2 * (unsigned)W);
-            slots = slots < CW_MIN_SLOTS ? CW_MIN_SLOTS : (slots > (unsigned)TS ? (unsigned)TS : slots);
+            // every root takes the whole table: at the low load this leaves
+            // (W / 1536 on the 6 KB table, about 0.2 on ER n = 1e6) a warp's
+            // slowest insert needs fewer probes, which paid more (k_c4_warp
+            // 1.58 -> 1.35 ms there) than the larger clear and sweep cost
+            const unsigned slots = (unsigned)TS;
             if constexpr (SPLIT) {
                 const SplitTab T{sk, sc, slots, nullptr};
                 c4_root<false>(g, vacc, u, b, din, T, 0, 1, lane, 32, S.seg, S.pv, S.dups, rc, W);
