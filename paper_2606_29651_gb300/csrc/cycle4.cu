@@ -208,6 +208,17 @@ struct SplitTab {
         }
         return -1;
     }
+    // Counts w (warp tier); true for the one call whose increment takes
+    // w's count from 1 to 2, so that each repeated key is reported once.
+    __device__ __forceinline__ bool add_rep(int w) const {
+        unsigned s = fib_slot(w, size);
+        for (unsigned probe = 0; probe < size; ++probe) {
+            const int prev = atomicCAS(&hk[s], -1, w);
+            if (prev == -1 || prev == w) return atomicAdd(&hc[s], 1) == 1;
+            s = next_probe(s, probe, w, size);
+        }
+        return false;
+    }
     __device__ __forceinline__ int get(int w) const {
         unsigned s = fib_slot(w, size);
         for (unsigned probe = 0; probe < size; ++probe) {
@@ -246,6 +257,17 @@ struct PackedTab {
         }
         return -1;
     }
+    __device__ __forceinline__ bool add_rep(int w) const {
+        const unsigned key = static_cast<unsigned>(w);
+        unsigned s = fib_slot(w, size);
+        for (unsigned probe = 0; probe < size; ++probe) {
+            const unsigned prev = atomicCAS(&t[s], EMPTY, (key << cb) | 1u);
+            if (prev == EMPTY) return false;
+            if ((prev >> cb) == key) return (atomicAdd(&t[s], 1u) & ((1u << cb) - 1)) == 1;
+            s = next_probe(s, probe, w, size);
+        }
+        return false;
+    }
     __device__ __forceinline__ int get(int w) const {
         const unsigned key = static_cast<unsigned>(w);
         unsigned s = fib_slot(w, size);
@@ -272,7 +294,9 @@ struct PackedTab {
 // A repeated key is a 4-cycle, so roots without one skip the credit and
 // middle passes. A CTA records the slots it fills in `touched` (flags[0]
 // counts them, flags[1] notes a repeated key) and empties only those; a warp
-// keeps no list: it uses its whole table for every root and sweeps it.
+// keeps no list of slots: it uses its whole table for every root, clears all
+// of it, and has each repeated key reported by the insert that makes its
+// count 2.
 // pv holds the per-middle-vertex sums of one chunk (per warp, or shared by
 // the CTA).
 template <bool CTA, class Tab>
@@ -284,13 +308,19 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     auto sync = [] {
         if (CTA) __syncthreads(); else __syncwarp();
     };
-    bool dup_l = false;   // warp group: this lane saw a repeated key
+    int nrep = 0;   // warp group: repeated keys, the first CW_DUPS of them listed in flags[]
     auto insert = [&](bool act, int, int w) {
-        const int slot = act ? T.add(w) : -2;
         if (!CTA) {
-            dup_l |= slot == -1;
+            const bool rep = act && T.add_rep(w);
+            const unsigned r = __ballot_sync(FULL, rep);
+            if (r) {
+                const int at = nrep + __popc(r & lanemask_lt());
+                if (rep && at < CW_DUPS) flags[at] = w;
+                nrep += __popc(r);
+            }
             return;
         }
+        const int slot = act ? T.add(w) : -2;
         // new keys of the warp take consecutive `touched` entries
         const unsigned fresh = __ballot_sync(FULL, slot >= 0);
         const unsigned dups = __ballot_sync(FULL, slot == -1);
@@ -308,31 +338,34 @@ __device__ __forceinline__ void c4_root(const Graph &g, VAcc *vacc, int u, int b
     sync();
     const int nt = CTA ? flags[0] : (int)T.size;   // entries of the list, or slots swept
     bool sweep = CTA ? flags[1] != 0 : false;
-    if (!CTA && __any_sync(FULL, dup_l)) {
-        // A warp sweeps its table for the repeated keys (count >= 2), credits
-        // them, and lists up to CW_DUPS of them in flags[]; the middle
-        // vertices of key w are N-(u) ∩ N(w), found by searching row w for
-        // each in-neighbour (one search per lane and pair), while the pairs
-        // number at most W / 4: each search is a short chain of dependent
-        // loads, and a root of a small dense graph with tens of repeated keys
-        // walks its few windows again sooner. Otherwise: the middle walk below.
+    if (!CTA && nrep > 0) {
+        // The repeated keys (count >= 2) of a warp's root were reported once
+        // each during the walk; up to CW_DUPS of them are listed in flags[],
+        // which gives their final counts without sweeping the table (more:
+        // a sweep). Each is credited C(c, 2); the middle vertices of key w
+        // are N-(u) ∩ N(w), found by searching row w for each in-neighbour
+        // (one search per lane and pair), while the pairs number at most
+        // W / 4: each search is a short chain of dependent loads, and a root
+        // of a small dense graph with tens of repeated keys walks its few
+        // windows again sooner. Otherwise: the middle walk below.
         long long su = 0;
-        int nd = 0;
-        for (int i0 = 0; i0 < nt; i0 += 32) {   // all lanes take part in every ballot
-            const int i = i0 + lane;
-            const int c = (i >= nt || T.empty(i)) ? 0 : T.cnt(i);
-            const unsigned rep = __ballot_sync(FULL, c >= 2);
-            if (c >= 2) {
-                const int w = T.key(i);
+        const int nd = nrep;
+        if (nd <= CW_DUPS) {
+            for (int k = lane; k < nd; k += 32) {
+                const int w = flags[k], c = T.get(w);
+                flags[CW_DUPS + k] = c;
                 su += c2(c);
                 add64(&vacc[w].C4, c2(c));
-                const int k = nd + __popc(rep & lanemask_lt());
-                if (k < CW_DUPS) {
-                    flags[k] = w;
-                    flags[CW_DUPS + k] = c;
+            }
+        } else {
+            for (int i = lane; i < nt; i += 32) {
+                if (T.empty(i)) continue;
+                const int c = T.cnt(i);
+                if (c >= 2) {
+                    su += c2(c);
+                    add64(&vacc[T.key(i)].C4, c2(c));
                 }
             }
-            nd += __popc(rep);
         }
         su = warp_sum(su);
         if (lane == 0) add64(&vacc[u].C4, su);
