@@ -809,13 +809,18 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
     // The wedges of elements [e0, e1) of the tile's concatenation of runs,
     // chunk by chunk of 32 in-neighbours: f(act, q, w) per wedge, done(v)
     // after each chunk.
-    auto visit = [&](long long e0, long long e1, int total, auto f, auto done) {
-        if (e0 >= e1) return;
-        int c = 0, top = nch;   // last chunk whose first run starts at or before e0
+    // c0: the last chunk whose first run starts at or before e0 (first_chunk)
+    auto first_chunk = [&](long long e0) {
+        int c = 0, top = nch;
         while (top - c > 1) {
             const int mid = (c + top) >> 1;
             if (offset(mid * 32) <= e0) c = mid; else top = mid;
         }
+        return c;
+    };
+    auto visit = [&](long long e0, long long e1, int total, int c0, auto f, auto done) {
+        if (e0 >= e1) return;
+        int c = c0;
         int r = c / RC, left = RC - (c - r * RC);   // warp range of chunk c, chunks left in it
         for (; c < nch; ++c) {
             const int p = c * 32 + lane;
@@ -880,7 +885,8 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
         // every warp takes an equal slice of the tile's wedges
         const long long e0 = (long long)total * wid / CK_NW, e1 = (long long)total * (wid + 1) / CK_NW;
         // 1. count the tile's wedges
-        visit(e0, e1, total, [&](bool ok, int, int w) {
+        const int c0 = e0 < e1 ? first_chunk(e0) : 0;   // the same for both walks of the slice
+        visit(e0, e1, total, c0, [&](bool ok, int, int w) {
             if (ok && (unsigned)(w - lo) < (unsigned)nk) T.add(w - lo);   // always, for a simple graph
         }, [](int) {});
         __syncthreads();
@@ -904,7 +910,7 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
             }
         }
         // 3. middle vertices: c - 1 per wedge, summed per in-neighbour
-        visit(e0, e1, total, [&](bool ok, int q, int w) {
+        visit(e0, e1, total, c0, [&](bool ok, int q, int w) {
             const bool in = ok && (unsigned)(w - lo) < (unsigned)nk;
             add_middle(pv, q, in ? T.get(w - lo) : 0);
         }, [&](int v) {
