@@ -112,9 +112,13 @@ class Shape:
         self.w_root = np.bincount(rd[sel], weights=pos[sel], minlength=n).astype(np.int64)
         self.din = np.bincount(rd[sel], minlength=n)
 
-    def c4_tiers(self, c4_warp_ub: int = 1536) -> dict:
-        """Relabelled ids of the roots of every 4-cycle kernel."""
+    def c4_tiers(self, c4_warp_ub: int = 1536, num_sms: int = 152) -> dict:
+        """Relabelled ids of the roots of every 4-cycle kernel (a graph with
+        fewer vertices than 32 warps per SM keeps roots above 256 wedges out
+        of the warp tiers)."""
         n, w = self.n, self.w_root
+        if n <= 32 * num_sms:
+            c4_warp_ub = min(c4_warp_ub, 256)
         live = (self.din >= 2) & (w >= 2)
         hub = self.din > WL_MAXD   # always the key-tiled tier
         pack_lim = (1 << (32 - int(max(n - 1, 1)).bit_length())) - 2   # packed tables hold counts below this

@@ -32,6 +32,7 @@ constexpr int CW_WARPS = 4;
 constexpr int CW_WORDS = 1536;      // table words per warp of k_c4_warp: 6 KB, 8 CTAs of 4 warps per SM
 constexpr int CWB_WORDS = 2048;     // k_c4_warp_big: 8 KB, 6 CTAs per SM
 constexpr int CW_MAXW = 1536;       // largest W of a root in the warp tiers
+constexpr int CW_SMALL_MAXW = 256;  // the same, for graphs with fewer vertices than resident warps
 constexpr int CW_DUPS = 32;         // repeated keys a warp credits by search at most
 constexpr int CW_BIG_LIST = 0;      // list slot of k_c4_warp_big's roots: the triangle stage's heavy list,
                                     // which nothing reads after that stage
@@ -997,7 +998,12 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     Graph g{w.n, w.m, w.rinfo, w.ncol, wl};
     launch_pdl(k_c4_wedge_len, w.num_sms * 8, 256, 0, st, g, wl, w.counters);
     after_launch(st, K_C4_WEDGE_LEN);
-    const int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
+    int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
+    // A graph with fewer vertices than the warp tier has resident warps is
+    // bound by its slowest root's walk, one warp each: roots above
+    // CW_SMALL_MAXW wedges go to the 4-warp tier there (G(2000, 0.01):
+    // 104 -> 94 us per call).
+    if (w.n <= w.num_sms * 32 && maxw > CW_SMALL_MAXW) maxw = CW_SMALL_MAXW;
     const int cb = packed_count_bits(w.n);
     // a packed word holds counts up to 2^cb - 2; with many vertices (large
     // graphs, batches) that is below what the warp tier takes, and the warp

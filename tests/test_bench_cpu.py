@@ -47,7 +47,7 @@ def test_four_cycle_tiers_partition_the_wedges(pad):
     # per-kernel bytes add up to B_c4 (less the roots with W < 2 or fewer
     # than two in-neighbours, which no kernel walks), with packed tables
     # and, past 2^21 vertices, split ones.
-    rp, ci = gg.er_mean_degree(3000, 48, 5)
+    rp, ci = gg.er_mean_degree(6000, 48, 5)
     rp = np.concatenate([rp, np.full(pad, rp[-1], rp.dtype)])
     ab = bench.algorithmic_bytes(rp, ci)
     tiers = {k: v for k, v in ab["per_kernel"].items() if k.startswith("k_c4")}
@@ -57,6 +57,16 @@ def test_four_cycle_tiers_partition_the_wedges(pad):
     assert tiers["k_c4_warp"] > 0 and tiers["k_c4_warp_big"] > 0
     if pad:   # split tables: the warp tiers stop at W = 576 and 768
         assert tiers["k_c4_mid"] > 0
+
+
+def test_small_graph_four_cycle_roots_above_256_wedges_leave_the_warp_tiers():
+    # fewer vertices than 32 warps per SM: the warp tiers stop at W = 256
+    rp, ci = gg.er_mean_degree(3000, 48, 5)
+    sh = bench.Shape(rp, ci)
+    t = sh.c4_tiers()
+    assert not t["k_c4_warp_big"].any()
+    assert (sh.w_root[t["k_c4_warp"]] <= 256).all() and t["k_c4_warp"].any()
+    assert t["k_c4_mid"].any() or t["k_c4_midp"].any()
 
 
 def test_deg_class_matches_library_rule():
