@@ -537,6 +537,7 @@ def run_batched(ni, torch, dev, stream, timer, steps, count) -> dict:
     ni.check()
     ref = out.clone()
     ms_eager = statistics.mean(timer.run(fn, steps))
+    kern = traced_kernel_ms(ni, fn, timer, 2)
     side = torch.cuda.Stream(dev)
     side.wait_stream(stream)
     g = torch.cuda.CUDAGraph()
@@ -564,6 +565,7 @@ def run_batched(ni, torch, dev, stream, timer, steps, count) -> dict:
             "graphs_per_s_one_per_launch": count / (ms_single * 1e-3), "ms_batched": ms_eager,
             "ms_cuda_graph": ms_graph, "ms_one_per_launch": ms_single, "replay_bit_exact": replay_same,
             "batched_equals_one_per_launch": bool(same_alone),
+            "kernel_ms": {k: round(v[0], 4) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])},
             "_parity_input": (graphs, ref.cpu().numpy(), vo)}
 
 

@@ -204,6 +204,90 @@ __global__ void __launch_bounds__(RL_THREADS) k_class_scatter(int n, int2 *vinfo
     }
 }
 
+// The class order of a graph of at most RL_TILE vertices in one CTA, with no
+// launch in between: the degree pass and class histogram of k_class_hist,
+// the scan of the class offsets, the stable class scatter of k_class_scatter
+// and the scan of the new degrees into the new row offsets (nrow[n] = m).
+constexpr int RS_THREADS = 1024;
+__global__ void __launch_bounds__(RS_THREADS) k_class_small(const int *rowptr, int n, int m, int2 *vinfo, int *coff,
+                                                            int *perm, int *nrow, int *counters, int *status) {
+    pdl_begin();
+    constexpr int NW = RS_THREADS / 32;
+    __shared__ int h[NCLASS];          // class counts, then each class's next id
+    __shared__ int wc[NW][NCLASS];     // per-warp class counts, then offsets
+    __shared__ int deg[RL_TILE];       // degree of each vertex
+    __shared__ int nd[RL_TILE];        // degree of each new id
+    __shared__ int wsum[32];
+    __shared__ int tot, smax;
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    for (int c = threadIdx.x; c < NCLASS; c += RS_THREADS) h[c] = 0;
+    if (threadIdx.x == 0) smax = 0;
+    __syncthreads();
+    int lmax = 0, bad = 0;
+    for (int x = threadIdx.x; x < n; x += RS_THREADS) {
+        const int a = rowptr[x], b = rowptr[x + 1];
+        const bool ok = a >= 0 && b >= a && b <= m;
+        const int d = ok ? b - a : 0;
+        if (!ok || (x == 0 && a != 0) || (x == n - 1 && b != m)) bad = 1;
+        deg[x] = d;
+        atomicAdd(&h[deg_class(d)], 1);
+        lmax = max(lmax, d);
+    }
+    if (bad) set_status(status, ST_EINVAL);
+    lmax = warp_max(lmax);
+    if (lane == 0) atomicMax(&smax, lmax);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicMax(&counters[CNT_DMAX], smax);
+        if (smax > MAX_DEGREE) set_status(status, ST_EOVERFLOW);
+    }
+    {   // class offsets (NCLASS <= RS_THREADS)
+        const int ex = block_exclusive_scan(threadIdx.x < NCLASS ? h[threadIdx.x] : 0, wsum, &tot);
+        if (threadIdx.x < NCLASS) {
+            h[threadIdx.x] = ex;
+            coff[threadIdx.x] = ex;
+        }
+    }
+    // new ids: stable rank by old id within the class, RS_THREADS vertices at a time
+    for (int x0 = 0; x0 < n; x0 += RS_THREADS) {
+        for (int i = threadIdx.x; i < NW * NCLASS; i += RS_THREADS) (&wc[0][0])[i] = 0;
+        __syncthreads();
+        const int x = x0 + threadIdx.x;
+        const bool valid = x < n;
+        const int d = valid ? deg[x] : 0;
+        const int c = valid ? deg_class(d) : NCLASS + lane;   // invalid lanes match only themselves
+        const unsigned peers = __match_any_sync(FULL, c);
+        const int rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) wc[w][c] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < NCLASS) {
+            int run = h[threadIdx.x];
+            for (int ww = 0; ww < NW; ++ww) {
+                const int t = wc[ww][threadIdx.x];
+                wc[ww][threadIdx.x] = run;
+                run += t;
+            }
+            h[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (valid) {
+            const int id = wc[w][c] + rank;
+            vinfo[x] = make_int2(id, d);
+            perm[id] = x;
+            nd[id] = d;
+        }
+        __syncthreads();
+    }
+    int carry = 0;   // new row offsets
+    for (int i0 = 0; i0 < n; i0 += RS_THREADS) {
+        const int i = i0 + threadIdx.x;
+        const int ex = block_exclusive_scan(i < n ? nd[i] : 0, wsum, &tot);
+        if (i < n) nrow[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) nrow[n] = carry;
+}
+
 // Union id of a column entry: graphs of a batch store ids local to the graph,
 // whose vertices occupy [vr.x, vr.y) of the union; -1 if out of range.
 __device__ __forceinline__ int global_id(int y, int2 vr, int n) {
@@ -417,13 +501,19 @@ __global__ void __launch_bounds__(RLC_THREADS) k_relabel_rows_cta(const int *row
 
 static void relabel_common(const int *rowptr, const int *colidx, const int2 *vrange, Work &w, cudaStream_t st) {
     const int nt = w.ntiles;
-    launch_pdl(k_class_hist, nt, RL_THREADS, 0, st, rowptr, w.n, w.m, w.vinfo, w.chist, nt, w.counters, w.status);
-    after_launch(st, K_CLASS_HIST);
-    launch_exclusive_scan(w.chist, w.coff, (long long)NCLASS * nt, false, w.scan_part, st);
-    // ndeg (degree of each new id) is staged in `split`, then scanned into nrow
-    launch_pdl(k_class_scatter, nt, RL_THREADS, 0, st, w.n, w.vinfo, w.coff, nt, w.perm, w.split);
-    after_launch(st, K_CLASS_SCATTER);
-    launch_exclusive_scan(w.split, w.nrow, w.n, true, w.scan_part, st);
+    if (nt == 1) {   // one tile: the class order in one launch
+        launch_pdl(k_class_small, 1, RS_THREADS, 0, st, rowptr, w.n, w.m, w.vinfo, w.coff, w.perm, w.nrow, w.counters,
+                   w.status);
+        after_launch(st, K_CLASS_HIST);
+    } else {
+        launch_pdl(k_class_hist, nt, RL_THREADS, 0, st, rowptr, w.n, w.m, w.vinfo, w.chist, nt, w.counters, w.status);
+        after_launch(st, K_CLASS_HIST);
+        launch_exclusive_scan(w.chist, w.coff, (long long)NCLASS * nt, false, w.scan_part, st);
+        // ndeg (degree of each new id) is staged in `split`, then scanned into nrow
+        launch_pdl(k_class_scatter, nt, RL_THREADS, 0, st, w.n, w.vinfo, w.coff, nt, w.perm, w.split);
+        after_launch(st, K_CLASS_SCATTER);
+        launch_exclusive_scan(w.split, w.nrow, w.n, true, w.scan_part, st);
+    }
     const int lrc = w.tune[TUNE_LONG_ROW_CLASS];
     // more CTAs than an SM holds: with rows of uneven length, the later
     // waves act as load balancing
