@@ -325,6 +325,56 @@ __global__ void __launch_bounds__(256) k_relabel_rows_warp(const int *rowptr, co
         const int ob = d > 0 ? rowptr[x] : 0;
         const int nb = nrow[r];
         const int2 vr = vrange ? vrange[x] : make_int2(0, n);
+        if (d <= 32) {
+            // One entry per lane: its place in the relabelled row is the
+            // number of entries of a lower class plus those of its class
+            // before it, from eight ballots over the class bits (inactive
+            // lanes take class NCLASS, above every real one).
+            const bool act = lane < d;
+            const int y = act ? colidx[ob + lane] : 0;
+            const int yp = __shfl_up_sync(FULL, y, 1);
+            int nid = 0, c = NCLASS;
+            unsigned dl = 0, bl = 0;
+            long long p6l = 0;
+            if (act) {
+                int ys = global_id(y, vr, n);
+                if (ys < 0) { bad |= ST_EINVAL; ys = x; }
+                else if (ys == x || (lane > 0 && y <= yp)) bad |= ST_ENOTSIMPLE;
+                const int2 vi = vinfo[ys];
+                nid = vi.x;
+                c = deg_class(vi.y);
+                dl = (unsigned)vi.y;
+                p6l = c2m1(vi.y);
+                bl = vi.x < r;
+            }
+            static_assert(NCLASS < 256, "classes and the inactive value NCLASS fit eight bits");
+            unsigned eq = FULL, lt = 0;
+#pragma unroll
+            for (int bit = 7; bit >= 0; --bit) {
+                const bool one = (c >> bit) & 1;
+                const unsigned ones = __ballot_sync(FULL, one);
+                if (one) {
+                    lt |= eq & ~ones;
+                    eq &= ones;
+                } else {
+                    eq &= ~ones;
+                }
+            }
+            if (act) ncol[nb + __popc(lt) + __popc(eq & lanemask_lt())] = nid;
+            // neighbour degrees are at most MAX_DEGREE: 32 of them fit 32 bits
+            const long long s1 = __reduce_add_sync(FULL, dl);
+            const int below = (int)__reduce_add_sync(FULL, bl);
+            const long long p6 = warp_sum(p6l);
+            const int sp = nb + below;
+            if (lane == 0) {
+                rinfo[r] = make_int4(nb, sp, nb + d, 0);
+                VAcc a;
+                a.S1 = s1; a.A1 = 0; a.P6 = p6; a.A2 = 0; a.A3 = 0; a.D12 = 0; a.K4 = 0; a.C4 = 0;
+                vacc[r] = a;
+            }
+            if (sp + lane < nb + d) tcnt[sp + lane] = 0;
+            continue;
+        }
         for (int c = lane; c < NCLASS; c += 32) H[c] = 0;
         __syncwarp();
         long long s1 = 0, p6 = 0;
