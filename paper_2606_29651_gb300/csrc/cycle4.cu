@@ -79,18 +79,20 @@ __device__ __forceinline__ int2 wedge_seg(const Graph &g, int u, int din, int p)
 }
 
 // The wedge segment of every in-entry of the rows with at most WL_MAXD
-// in-neighbours, a half-warp per row: the row gather and binary search of
-// each entry, made here with every thread independent, so that the
-// per-root kernels read one coalesced 8-byte entry per in-neighbour.
+// in-neighbours, a group of L lanes per row (16, or 8 for graphs of mean
+// degree below 16): the row gather and binary search of each entry, made
+// here with every thread independent, so that the per-root kernels read one
+// coalesced 8-byte entry per in-neighbour.
+template <int L>
 __global__ void __launch_bounds__(256, 8) k_c4_wedge_len(Graph g, int2 *wl, const int *counters) {
     pdl_begin();
     if (degree_overflow(counters)) return;
-    const int hl = threadIdx.x & 15;
-    const int gh = (blockIdx.x * blockDim.x + threadIdx.x) >> 4, nh = (gridDim.x * blockDim.x) >> 4;
+    const int hl = threadIdx.x & (L - 1);
+    const int gh = (blockIdx.x * blockDim.x + threadIdx.x) / L, nh = (gridDim.x * blockDim.x) / L;
     for (int u = gh; u < g.n; u += nh) {
         const int4 ru = g.rinfo[u];
         if (ru.y - ru.x > WL_MAXD) continue;
-        for (int p = ru.x + hl; p < ru.y; p += 16) {
+        for (int p = ru.x + hl; p < ru.y; p += L) {
             const int4 rv = g.rinfo[g.ncol[p]];
             wl[p] = make_int2(rv.x, wedge_len(g, u, rv));
         }
@@ -996,7 +998,8 @@ void launch_cycle4(Work &w, cudaStream_t st) {
     // the wedge segments take the region of the triangle counts, dead after the aggregate stage
     int2 *wl = reinterpret_cast<int2 *>(w.tcnt);
     Graph g{w.n, w.m, w.rinfo, w.ncol, wl};
-    launch_pdl(k_c4_wedge_len, w.num_sms * 8, 256, 0, st, g, wl, w.counters);
+    if ((long long)w.m < 16ll * w.n) launch_pdl(k_c4_wedge_len<8>, w.num_sms * 8, 256, 0, st, g, wl, w.counters);
+    else launch_pdl(k_c4_wedge_len<16>, w.num_sms * 8, 256, 0, st, g, wl, w.counters);
     after_launch(st, K_C4_WEDGE_LEN);
     int maxw = w.tune[TUNE_C4_WARP_MAXW] < CW_MAXW ? w.tune[TUNE_C4_WARP_MAXW] : CW_MAXW;
     // A graph with fewer vertices than the warp tier has resident warps is
