@@ -680,10 +680,15 @@ __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, cons
 // in-neighbour, |E| = m / 2 of them.
 constexpr int CK_THREADS = 1024;
 constexpr int CK_NW = CK_THREADS / 32;
-constexpr int CK_WORDS = 48 * 1024;                 // counter words in shared memory (192 KB)
+constexpr size_t CK_OTHER = CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + 64 * 4;   // segment tables, sums, scalars
+// Counter words (204 KB; tiles of 104448 keys with 16-bit counters). Larger
+// tiles pay, as every tile costs passes over the in-neighbours: on R-MAT 22
+// the tier took 598 ms with 48K words, 587 with 50K, 567 with 51K, and
+// 571-572 with 51.5K and with all the 227 KB the rest leaves (52928).
+constexpr int CK_WORDS = 51 * 1024;
 constexpr int CK_NARROW_MAXD = 65534;               // in-degree up to which 16-bit counters cannot overflow
 constexpr int CK_INF = 0x7fffffff;
-constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + 64 * 4;
+constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_OTHER;
 static_assert(CK_SMEM <= 227 * 1024, "k_c4_tiled shared memory");
 
 // Root order of the key-tiled tier: the queued roots (list 4, their wedge
