@@ -1,13 +1,14 @@
 """Continuous-batching server for orbit-count requests.
 
-Requests (one graph each, CSR in host memory) arrive at any time. A
-scheduler thread admits them in arrival order while their device footprint
-fits a memory budget, packs every admitted group into one niorca_count_batch
-call on one of several CUDA streams, and keeps up to `streams` such batches
-in flight: graphs that arrive while others are on the GPU join the next batch
-as soon as a stream and enough memory are free, and its copies and kernels
-overlap with the batches already running. A request's latency runs from
-submit() to the moment its counts are in host memory.
+Requests (one graph each, CSR in host memory) arrive at any time. Each of
+`streams` worker threads owns a CUDA stream and its pinned staging buffers;
+a free worker admits the waiting requests in arrival order while their
+device footprint fits a memory budget, packs them into one
+niorca_count_batch call on its stream, waits for it, and hands out the
+counts. Graphs that arrive while the workers are busy join the next batch,
+and one worker's packing and copying out overlap with the others' batches on
+the GPU (no worker waits on another's host work). A request's latency runs
+from submit() to the moment its counts are in host memory.
 
 The counts of a graph do not depend on which other graphs share its batch
 (the batched call counts the disjoint union, and no graphlet spans two
@@ -83,8 +84,9 @@ class _Batch:
 class Server:
     """Continuous batching over `streams` CUDA streams within `mem_budget` bytes.
 
-    Batches pack their CSR and copy out their counts on a small thread pool;
-    a request's result is an int64 [n, 15] view of its batch's array.
+    Each stream has a worker thread; batches pack their CSR and copy out
+    their counts on a small shared thread pool when large. A request's
+    result is an int64 [n, 15] view of its batch's array.
     """
 
     PARALLEL_ENTRIES = 1 << 19   # CSR entries (or count words) from which a batch uses the pool
@@ -97,9 +99,7 @@ class Server:
         self.max_batch_edges = int(max_batch_edges)
         with torch.cuda.device(self.device):
             self.streams = [torch.cuda.Stream(self.device) for _ in range(streams)]
-        self._free_slots = [_Slot(st) for st in self.streams]
         self._pending: collections.deque = collections.deque()
-        self._inflight: list[_Batch] = []
         self._in_use = 0
         self._cv = threading.Condition()
         self._stop = False
@@ -107,8 +107,10 @@ class Server:
         self.batches = 0
         self._pool = ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1)),
                                         thread_name_prefix="niorca-pack")
-        self._thread = threading.Thread(target=self._loop, name="niorca-server", daemon=True)
-        self._thread.start()
+        self._workers = [threading.Thread(target=self._work, args=(_Slot(st),), name=f"niorca-stream{i}",
+                                          daemon=True) for i, st in enumerate(self.streams)]
+        for t in self._workers:
+            t.start()
 
     # -------------------------------------------------------------- client
     def submit(self, rowptr: np.ndarray, colidx: np.ndarray) -> Future:
@@ -128,9 +130,10 @@ class Server:
     def shutdown(self, wait: bool = True) -> None:
         with self._cv:
             self._stop = True
-            self._cv.notify()
+            self._cv.notify_all()
         if wait:
-            self._thread.join()
+            for t in self._workers:
+                t.join()
             self._pool.shutdown(wait=True)
 
     def __enter__(self):
@@ -139,9 +142,10 @@ class Server:
     def __exit__(self, *exc):
         self.shutdown()
 
-    # ----------------------------------------------------------- scheduler
+    # ------------------------------------------------------------- workers
     def _admit(self):
-        """Pop the longest prefix of the queue that fits the free memory."""
+        """Pop the longest prefix of the queue that fits the free memory
+        (called with the lock held)."""
         take, n, m = [], 0, 0
         while self._pending and len(take) < self.max_batch_graphs:
             r = self._pending[0]
@@ -157,8 +161,33 @@ class Server:
             m += r.m
         return take, footprint(len(take), n, m) if take else 0
 
-    def _launch(self, reqs, nbytes):
-        slot = self._free_slots.pop()
+    def _work(self, slot):
+        torch.cuda.set_device(self.device)
+        while True:
+            with self._cv:
+                while True:
+                    reqs, nbytes = self._admit() if self._pending else ([], 0)
+                    if reqs:
+                        self._in_use += nbytes
+                        self.batches += 1
+                        break
+                    if self._stop and not self._pending:
+                        return
+                    self._cv.wait(timeout=0.05)
+            try:
+                b = self._launch(slot, reqs, nbytes)
+                b.event.synchronize()
+                self._retire(b, time.perf_counter())
+            except Exception as e:   # the call itself failed (e.g. no device memory)
+                for r in reqs:
+                    if not r.future.done():
+                        r.t_done = time.perf_counter()
+                        r.future.set_exception(e)
+            with self._cv:
+                self._in_use -= nbytes
+                self._cv.notify_all()   # memory is free again
+
+    def _launch(self, slot, reqs, nbytes):
         stream = slot.stream
         b = _Batch(reqs, slot, nbytes)
         ns = np.array([r.n for r in reqs], dtype=np.int64)
@@ -193,9 +222,7 @@ class Server:
             b.event.record(stream)
         b.host_out = host_out
         b.keep = (d_rp, d_ci, d_off, out, vo)
-        self._in_use += nbytes
-        self._inflight.append(b)
-        self.batches += 1
+        return b
 
     def _runs(self, fn, offsets):
         """fn(lo, hi) over the requests of a batch; a batch with many entries
@@ -239,15 +266,14 @@ class Server:
                 out[lo:hi] = res[lo:hi]
 
             self._ranges(unpack, total_n, 15 * total_n)
+        b.keep = None
         if err is not None and len(b.reqs) > 1 and err.status != _lib.Status.ECUDA:
             # a malformed graph fails the whole batch: run each request alone
             with self._cv:
                 for r in reversed(b.reqs):
                     r.alone = True
                     self._pending.appendleft(r)
-            self._in_use -= b.nbytes
-            self._free_slots.append(b.slot)
-            b.keep = None
+                self._cv.notify_all()
             return
         for g, r in enumerate(b.reqs):
             r.t_done = now
@@ -255,35 +281,8 @@ class Server:
                 r.future.set_exception(err)
             else:
                 r.future.set_result(out[vo[g]:vo[g + 1]])
-        self.completed += len(b.reqs)
-        self._in_use -= b.nbytes
-        self._free_slots.append(b.slot)
-        b.keep = None
-
-    def _loop(self):
-        torch.cuda.set_device(self.device)
-        while True:
-            with self._cv:
-                if self._stop and not self._pending and not self._inflight:
-                    return
-                if not self._pending and not self._inflight:
-                    self._cv.wait(timeout=0.05)
-                    continue
-            now = time.perf_counter()
-            for b in [b for b in self._inflight if b.event.query()]:
-                self._inflight.remove(b)
-                self._retire(b, now)
-            launched = False
-            with self._cv:
-                if self._pending and self._free_slots:
-                    reqs, nbytes = self._admit()
-                else:
-                    reqs, nbytes = [], 0
-            if reqs:
-                self._launch(reqs, nbytes)
-                launched = True
-            if not launched:
-                time.sleep(20e-6)
+        with self._cv:
+            self.completed += len(b.reqs)
 
 
 def latency_stats(requests_latency_s) -> dict:
