@@ -668,7 +668,9 @@ __global__ void __launch_bounds__(CC_THREADS) k_c4_cta(Graph g, VAcc *vacc, cons
 // first finds every in-neighbour's run (a galloping search from the cursor,
 // one thread per in-neighbour) and its offset in the concatenation of the
 // tile's runs (a prefix sum across the CTA); every warp then takes an equal
-// slice of that concatenation, so that hub rows do not leave warps waiting.
+// slice of that concatenation, weighted so that each chunk of 32
+// in-neighbours also counts for its overhead, and neither hub rows nor many
+// short runs leave warps waiting.
 // It counts the slice's wedges, credits C(c, 2) to every key w and to u
 // from the counts, walks the slice again adding c - 1 per wedge to its
 // middle vertex, moves the cursors past the runs, and clears. The next tile
@@ -688,6 +690,12 @@ constexpr size_t CK_OTHER = CK_NW * sizeof(SegTab) + CK_NW * 32 * 8 + 64 * 4;   
 constexpr int CK_WORDS = 51 * 1024;
 constexpr int CK_NARROW_MAXD = 65534;               // in-degree up to which 16-bit counters cannot overflow
 constexpr int CK_INF = 0x7fffffff;
+// Weight of a chunk's overhead in elements when the walks are cut into warp
+// slices: equal element counts left the warps of a tile with many short runs
+// waiting at the tile barriers for the warp with the most chunks (R-MAT 22:
+// 566 ms with equal elements; 430, 398, 372, 363, 367, 371, 392 ms with
+// weights 32, 64, 128, 256, 384, 512, 1024).
+constexpr int CK_ALPHA = 256;
 constexpr size_t CK_SMEM = (size_t)CK_WORDS * 4 + CK_OTHER;
 static_assert(CK_SMEM <= 227 * 1024, "k_c4_tiled shared memory");
 
@@ -817,13 +825,22 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
     // The wedges of elements [e0, e1) of the tile's concatenation of runs,
     // chunk by chunk of 32 in-neighbours: f(act, q, w) per wedge, done(v)
     // after each chunk.
-    // c0: the last chunk whose first run starts at or before e0 (first_chunk)
-    auto first_chunk = [&](long long e0) {
+    // Slices by weight: each chunk of 32 in-neighbours counts CK_ALPHA
+    // elements of overhead ahead of its elements (its cursor loads, table
+    // and window setup), so that a slice across many short runs gets fewer
+    // elements. weighted() gives the chunk holding weighted position wp and
+    // the element there.
+    auto weighted = [&](long long wp, int total, long long &e) {
         int c = 0, top = nch;
         while (top - c > 1) {
             const int mid = (c + top) >> 1;
-            if (offset(mid * 32) <= e0) c = mid; else top = mid;
+            if (offset(mid * 32) + (long long)CK_ALPHA * mid <= wp) c = mid; else top = mid;
         }
+        const long long zc = offset(c * 32);
+        const long long zn = c + 1 < nch ? offset((c + 1) * 32) : total;
+        const long long x = wp - zc - (long long)CK_ALPHA * c - CK_ALPHA;
+        e = zc + (x > 0 ? x : 0);
+        if (e > zn) e = zn;
         return c;
     };
     auto visit = [&](long long e0, long long e1, int total, int c0, auto f, auto done) {
@@ -890,10 +907,14 @@ __device__ __forceinline__ void c4_tiled_root(const Graph &g, VAcc *vacc, int u,
             __syncthreads();
         }
         const int total = *s_tot;
-        // every warp takes an equal slice of the tile's wedges
-        const long long e0 = (long long)total * wid / CK_NW, e1 = (long long)total * (wid + 1) / CK_NW;
+        // every warp takes an equal slice of the tile's weighted wedges (the
+        // same slice for both walks)
+        const long long wt = (long long)total + (long long)CK_ALPHA * nch;
+        long long e0, e1;
+        const int c0 = weighted(wt * wid / CK_NW, total, e0);
+        weighted(wt * (wid + 1) / CK_NW, total, e1);
+        if (wid == CK_NW - 1) e1 = total;
         // 1. count the tile's wedges
-        const int c0 = e0 < e1 ? first_chunk(e0) : 0;   // the same for both walks of the slice
         visit(e0, e1, total, c0, [&](bool ok, int, int w) {
             if (ok && (unsigned)(w - lo) < (unsigned)nk) T.add(w - lo);   // always, for a simple graph
         }, [](int) {});
