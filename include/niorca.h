@@ -25,7 +25,12 @@
  *     out[v * 15 + k] = psi_k(v). It is fully overwritten.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls
  *     only enqueue work; they never synchronise the stream. Results are valid
- *     once the stream has reached the end of the call's work.
+ *     once the stream has reached the end of the call's work. The kernels are
+ *     launched with programmatic dependent launch allowed: a kernel may be
+ *     scheduled while the one before it on the stream drains, and waits for
+ *     it to complete (griddepcontrol.wait) before it touches memory, so the
+ *     stream order with the caller's own work is unchanged. No kernel of the
+ *     library lets the work after it start early.
  *   - Argument errors are returned synchronously and nothing is enqueued.
  *     Errors found on the device (malformed CSR, too large a degree) are
  *     recorded in the status word of the call's stream, read by
