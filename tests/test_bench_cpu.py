@@ -59,6 +59,26 @@ def test_four_cycle_tiers_partition_the_wedges(pad):
         assert tiers["k_c4_mid"] > 0
 
 
+def test_hub_roots_go_to_the_key_tiled_tier():
+    # a root with more than 1024 in-neighbours is routed to the key-tiled
+    # tier whatever its wedge count (no one-warp search of its rows for W)
+    rp, ci = gg.er_mean_degree(6000, 4, 3)
+    n = len(rp) - 1
+    hub_edges = [(v, n) for v in range(0, 6000, 4)]   # 1500 neighbours, all below the hub in any order
+    rows = [list(ci[rp[v]:rp[v + 1]]) for v in range(n)] + [[]]
+    for v, h in hub_edges:
+        rows[v].append(h)
+        rows[h].append(v)
+    rp2 = np.zeros(n + 2, np.int64)
+    rp2[1:] = np.cumsum([len(r) for r in rows])
+    ci2 = np.concatenate([np.array(sorted(r), np.int32) for r in rows]).astype(np.int32)
+    sh = bench.Shape(rp2.astype(np.int32), ci2)
+    t = sh.c4_tiers()
+    hub = int(np.flatnonzero(sh.order == n)[0])   # relabelled id of the hub
+    assert sh.din[hub] > 1024 and t["k_c4_tiled"][hub]
+    assert not any(t[k][hub] for k in t if k != "k_c4_tiled")
+
+
 def test_small_graph_four_cycle_roots_above_256_wedges_leave_the_warp_tiers():
     # fewer vertices than 32 warps per SM: the warp tiers stop at W = 256
     rp, ci = gg.er_mean_degree(3000, 48, 5)
